@@ -1,0 +1,140 @@
+/*
+ * gv_oracle.h -- plain, slow FP64 CPU oracle of electromagnetic shower
+ * transport through a layered calorimeter (GeantV, arXiv:2005.00949).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library may include,
+ * link or call this code; only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark use it.  It shares no code with the CUDA
+ * path: every formula below is written out a second time, independently of
+ * the product's table builder.
+ *
+ * The paper (Sec. 3.5) defers its physics formulas to an external EM paper,
+ * so the physics implemented here is the textbook set listed in the design
+ * notes of this repository:
+ *   Compton          free-electron Klein-Nishina
+ *   photoelectric    Sauter-type K-shell formula x 5/4, photoelectron takes k
+ *   pair production  complete-screening Bethe-Heitler (Tsai)
+ *   bremsstrahlung   complete-screening (Tsai), discrete above the gamma cut
+ *   ionisation       Moller (e-) / Bhabha (e+), discrete above the e- cut;
+ *                    restricted Berger-Seltzer (ICRU 37) collision loss below
+ *   annihilation     Heitler two-photon, in flight and at rest
+ * The stepping loop follows the stage sequence of Sec. 2.1.2 (Fig. "simulation
+ * stages"): PreStep, ComputeIntLen, GeomQuery, Propagation, AlongStepAction,
+ * PostStepActions, SteppingActions; secondaries go to a LIFO stack (the
+ * StackBuffer of Sec. 2.1.2).  Random numbers come from Philox4x32-10 (the
+ * Random123 family of Sec. 3.3.2) keyed by (seed, event) and counted by
+ * (track id, step, block), which is the per-track stream idea of Sec. 5.1.
+ */
+#ifndef GV_ORACLE_H
+#define GV_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OR_MAX_ELEM 4
+#define OR_MAX_MAT 4
+#define OR_MAX_SUBSEQ 8
+#define OR_NCOUNT 12
+
+/* particle types */
+enum { OR_GAMMA = 0, OR_ELECTRON = 1, OR_POSITRON = 2 };
+
+/* process bits (process_mask) */
+enum {
+  OR_P_COMPTON = 1u << 0, OR_P_PHOTO = 1u << 1, OR_P_PAIR = 1u << 2,
+  OR_P_BREM = 1u << 3, OR_P_IONI = 1u << 4, OR_P_ANNIH = 1u << 5
+};
+
+/* alias-sampled final-state models */
+enum { OR_M_COMPTON = 0, OR_M_PAIR = 1, OR_M_BREM = 2, OR_M_MOLLER = 3,
+       OR_M_BHABHA = 4, OR_M_ANNIH = 5, OR_NMODEL = 6 };
+
+/* per-event counters written by or_transport */
+enum { OR_C_STEPS = 0, OR_C_STEPS_G, OR_C_STEPS_EM, OR_C_STEPS_EP,
+       OR_C_TRK_G, OR_C_TRK_EM, OR_C_TRK_EP, OR_C_PAIR, OR_C_ANNIH,
+       OR_C_EP_ESC, OR_C_UNSCAT, OR_C_SPARE };
+
+typedef struct {
+  int n_elem;
+  double Z[OR_MAX_ELEM], A[OR_MAX_ELEM], w[OR_MAX_ELEM]; /* w: mass fractions */
+  double rho;   /* g/cm3 */
+  double I_eV;  /* mean excitation energy */
+} or_material;
+
+typedef struct {
+  int n_mat;
+  or_material mat[OR_MAX_MAT];
+  int n_layers;                     /* repeated layers along +z from z=0 */
+  int n_sub;                        /* sub-slabs per layer */
+  double sub_thick[OR_MAX_SUBSEQ];  /* cm */
+  int sub_mat[OR_MAX_SUBSEQ];
+  double half_x, half_y;            /* cm; <= 0 means unbounded */
+  int nx, ny;                       /* scoring cells per layer (0: none) */
+  double gamma_cut, e_cut, track_cut; /* MeV */
+  unsigned process_mask;
+} or_setup;
+
+typedef struct {
+  int type;
+  double E;            /* kinetic energy, MeV */
+  double x, y, z;      /* cm */
+  double u, v, w;      /* unit direction */
+  uint32_t event;
+} or_primary;
+
+typedef struct or_ctx or_ctx;
+
+int or_create(const or_setup *s, or_ctx **out);
+void or_destroy(or_ctx *c);
+
+/* --- physics, exact (analytic or quadrature) -------------------------- */
+double or_material_X0(const or_ctx *c, int mat);          /* g/cm2 */
+double or_material_nel(const or_ctx *c, int mat);         /* electrons/cm3 */
+double or_klein_nishina_e(double k);                      /* cm2 per electron */
+double or_xs(const or_ctx *c, int type, int proc_index, int mat, double E); /* cm^-1 */
+double or_dedx(const or_ctx *c, int type, int mat, double E);   /* MeV/cm */
+double or_dedx_parts(const or_ctx *c, int type, int mat, double E, double cut_e, double cut_g,
+                     double *col, double *rad);
+double or_range_exact(const or_ctx *c, int type, int mat, double E);  /* cm */
+double or_dcs(int model, double E, double var, double cut); /* shape in physical variable */
+
+/* --- tables (nodes = exact values on the log grid) ------------------- */
+int or_grid_size(void);
+double or_grid_energy(int i);
+double or_table_node(const or_ctx *c, int type, int q, int mat, int i);
+double or_table_lookup(const or_ctx *c, int type, int q, int mat, double E);
+double or_eloss(const or_ctx *c, int type, int mat, double E, double s); /* post-step energy */
+
+/* --- alias sampling tables ------------------------------------------- */
+int or_alias_info(const or_ctx *c, int model, double *E_lo, int *n_E);
+int or_alias_table(const or_ctx *c, int model, int ie, double *pdf, float *q, int *alias);
+double or_alias_sample(const or_ctx *c, int model, double E, const double *u3, double *xi);
+
+/* --- RNG -------------------------------------------------------------- */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* --- geometry -------------------------------------------------------- */
+int or_n_subtotal(const or_ctx *c);
+double or_plane_z(const or_ctx *c, int k);
+int or_locate(const or_ctx *c, double z, double w);
+double or_distance(const or_ctx *c, const double pos[3], const double dir[3], int sub,
+                   int *next_sub, int *plane);
+
+/* --- interactions given uniforms (unit level) ------------------------ */
+int or_interact(const or_ctx *c, int type, int proc, double E, const double dir[3],
+                const double u[8], double *out /* 16 doubles */);
+
+/* --- full transport --------------------------------------------------- */
+int or_transport(const or_ctx *c, const or_primary *p, long n_prim, long n_events,
+                 uint64_t seed, double *edep /* [n_events][n_subtotal] */,
+                 double *cell_edep /* [n_layers][nx][ny] or NULL */,
+                 double *escape_E /* [n_events] */,
+                 long long *ev_counts /* [n_events][OR_NCOUNT] */,
+                 int n_threads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,494 @@
+"""Pins of the FP64 CPU oracle against things other than itself.
+
+Each test checks the oracle against a published value (golden files, each
+with its source), a closed form reached by a different route, an invariant
+(conservation laws, round trips), or brute force.  None of them needs a GPU.
+"""
+import dataclasses
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+from scipy import integrate, stats
+
+from conftest import golden_lines
+from paper_2005_00949_gb300 import workloads as W
+
+ME = 0.51099895
+RE = 2.8179403262e-13
+SIGMA_T = 8.0 * math.pi * RE * RE / 3.0
+
+
+def _material_from_golden(name, zs, as_, ws):
+    Z = [float(z) for z in zs.split(",")]
+    A = [float(a) for a in as_.split(",")]
+    w = [float(x) for x in ws.split(",")]
+    return W.Material(name, Z, A, w, 1.0, 75.0)
+
+
+def _oracle_for(oracle_mod, materials, **kw):
+    wl = dataclasses.replace(W.photon_slab(1), materials=materials, **kw)
+    return oracle_mod.Oracle(wl)
+
+
+# ----------------------------------------------------------------------------- RNG
+def test_philox_known_answers(oracle_mod):
+    """Philox4x32-10 reproduces the Random123 known-answer vectors."""
+    n = 0
+    for cols in golden_lines("philox_kat.txt"):
+        v = [int(x, 16) for x in cols]
+        out = oracle_mod.philox4x32_10(v[0:4], v[4:6])
+        assert out.tolist() == v[6:10]
+        n += 1
+    assert n == 3
+
+
+def test_philox_uniformity(oracle_mod):
+    """Top-24-bit uniforms: chi-square on 1024 bins and lag-1 correlation."""
+    u = []
+    key = [0x1234, 0x5678]
+    for i in range(20000):
+        o = oracle_mod.philox4x32_10([i, 7, 0, 0], key)
+        u.extend(((int(x) >> 8) + 1) / 16777216.0 for x in o)
+    u = np.array(u)
+    assert u.min() > 0.0 and u.max() <= 1.0
+    h, _ = np.histogram(u, bins=1024, range=(0.0, 1.0))
+    chi2 = ((h - len(u) / 1024) ** 2 / (len(u) / 1024)).sum()
+    assert stats.chi2.sf(chi2, 1023) > 1e-3
+    assert abs(np.corrcoef(u[:-1], u[1:])[0, 1]) < 5.0 / math.sqrt(len(u))
+
+
+# ----------------------------------------------------------------------------- materials
+def test_radiation_lengths_match_pdg(oracle_mod):
+    for cols in golden_lines("pdg_radiation_lengths.txt"):
+        name, zs, as_, ws, x0 = cols
+        o = _oracle_for(oracle_mod, [_material_from_golden(name, zs, as_, ws)])
+        got = o.X0(0)
+        # PDG prints 4 significant digits
+        assert abs(got - float(x0)) <= 0.006 * float(x0) / 6.0 + 0.005, (name, got, x0)
+
+
+# ----------------------------------------------------------------------------- Compton
+def test_klein_nishina_thomson_limit(oracle_mod):
+    """sigma_KN / sigma_T = 1 - 2k + 26/5 k^2 + O(k^3) for k = E/m -> 0
+    (k >= 0.002, i.e. above the 1 keV grid floor, where the closed form keeps
+    full FP64 accuracy)."""
+    for K in [2e-3, 4e-3, 1e-2]:
+        r = oracle_mod.klein_nishina_e(K * ME) / SIGMA_T
+        assert abs(r - (1 - 2 * K + 26.0 / 5.0 * K * K)) < 20 * K ** 3
+
+
+def test_klein_nishina_high_energy_limit(oracle_mod):
+    """sigma_KN -> pi r_e^2 / k (ln 2k + 1/2) for k >> 1."""
+    for K in [1e5, 1e6, 1e7]:
+        r = oracle_mod.klein_nishina_e(K * ME) / (math.pi * RE * RE / K * (math.log(2 * K) + 0.5))
+        assert abs(r - 1.0) < 5 * math.log(K) / K
+
+
+def test_klein_nishina_dcs_integrates_to_total(oracle_mod):
+    """Quadrature of the KN DCS in eps = k'/k equals the closed-form total."""
+    O = oracle_mod.Oracle
+    for k in [0.01, 0.1, 1.0, 10.0, 1000.0]:
+        K = k / ME
+        e0 = 1.0 / (1.0 + 2.0 * K)
+        # dsigma/deps = pi r_e^2 / K * (1/eps + eps - sin^2 theta)
+        val, _ = integrate.quad(lambda e: O.dcs(W_M.COMPTON, k, e), e0, 1.0, epsabs=0,
+                                epsrel=1e-11, limit=200, points=[math.sqrt(e0)])
+        tot = math.pi * RE * RE / K * val
+        assert abs(tot / oracle_mod.klein_nishina_e(k) - 1.0) < 1e-9
+
+
+def test_compton_water_matches_xcom(oracle_mod):
+    mats = [W.Material("water", [1.0, 8.0], [1.008, 15.999], [0.111894, 0.888106], 1.0, 75.0)]
+    o = _oracle_for(oracle_mod, mats)
+    (E, mu), = [tuple(map(float, c)) for c in golden_lines("xcom_water.txt")]
+    assert abs(o.xs(W.GAMMA, 0, 0, E) / 1.0 - mu) < 2e-3 * mu
+
+
+# ----------------------------------------------------------------------------- pair / brems
+class W_M:
+    COMPTON, PAIR, BREM, MOLLER, BHABHA, ANNIH = range(6)
+
+
+def test_pair_high_energy_limit_is_seven_ninths(oracle_mod):
+    o = oracle_mod.Oracle(W.pbps_electrons(1))
+    for m in (0, 1):
+        rho = o.wl.materials[m].rho
+        r = o.xs(W.GAMMA, 2, m, 1e6) * o.X0(m) / rho
+        assert abs(r - 7.0 / 9.0) < 2e-6
+        assert o.xs(W.GAMMA, 2, m, 2 * ME * 0.999) == 0.0
+
+
+def test_pair_total_is_dcs_quadrature(oracle_mod):
+    o = oracle_mod.Oracle(W.pbps_electrons(1))
+    for k in [1.1, 2.0, 10.0, 1e3]:
+        a = ME / k
+        val, _ = integrate.quad(lambda x: o.dcs(W_M.PAIR, k, x), a, 1 - a, epsrel=1e-12)
+        assert abs(o.xs(W.GAMMA, 2, 0, k) / (o.wl.materials[0].rho / o.X0(0)) - val) < 1e-12
+
+
+def test_brems_total_radiative_loss_is_E_over_X0(oracle_mod):
+    """With no photon cut the complete-screening loss approaches E/X0 (PDG)."""
+    o = oracle_mod.Oracle(W.pbps_electrons(1))
+    T = 1e6
+    _, col, rad = o.dedx_parts(W.ELECTRON, 0, T, 1.0, 1e30)
+    r = rad * o.X0(0) / o.wl.materials[0].rho / (T + ME)
+    assert abs(r - 1.0) < 1e-5
+
+
+def test_brems_discrete_and_restricted_match_dcs_quadrature(oracle_mod):
+    o = oracle_mod.Oracle(W.pbps_electrons(1))
+    kc = o.wl.gamma_cut
+    scale = o.wl.materials[0].rho / o.X0(0)
+    for T in [1.5, 10.0, 1e3, 1e5]:
+        disc, _ = integrate.quad(lambda k: o.dcs(W_M.BREM, T, k), kc, T, epsrel=1e-12, limit=200)
+        assert abs(o.xs(W.ELECTRON, 0, 0, T) / scale - disc) < 1e-10 * max(1.0, disc)
+        loss, _ = integrate.quad(lambda k: k * o.dcs(W_M.BREM, T, k), 0.0, min(kc, T), epsrel=1e-12)
+        _, _, rad = o.dedx_parts(W.ELECTRON, 0, T, 1.0, kc)
+        assert abs(rad / scale - loss) < 1e-10 * loss
+
+
+# ----------------------------------------------------------------------------- ionisation
+def test_collision_stopping_power_matches_estar(oracle_mod):
+    mats = [W.Material("water", [1.0, 8.0], [1.008, 15.999], [0.111894, 0.888106], 1.0, 75.0)]
+    o = _oracle_for(oracle_mod, mats, gamma_cut=1e30, e_cut=1e30)
+    for cols in golden_lines("estar_water.txt"):
+        if cols[0] == "range":
+            E, R = float(cols[1]), float(cols[2])
+            assert abs(o.range_exact(W.ELECTRON, 0, E) - R) < 2e-3 * R
+            continue
+        E, S = float(cols[0]), float(cols[1])
+        _, col, _ = o.dedx_parts(W.ELECTRON, 0, E, 1e30, 1e30)
+        assert abs(col - S) < 1e-3 * S, (E, col, S)
+
+
+@pytest.mark.parametrize("ptype,model", [(W.ELECTRON, W_M.MOLLER), (W.POSITRON, W_M.BHABHA)])
+def test_restricted_loss_derivative_is_delta_ray_dcs(oracle_mod, ptype, model):
+    """d(restricted dE/dx)/dTc = n_e Tc dsigma/dT_delta(Tc): ties the
+    Berger-Seltzer formula to the Moller / Bhabha differential cross section."""
+    o = oracle_mod.Oracle(W.pbps_electrons(1))
+    nel = o.n_el(0)
+    for T in [5.0, 50.0, 1000.0]:
+        for Tc in [0.3, 1.0, 2.0]:
+            h = 1e-6
+            d = (o.dedx_parts(ptype, 0, T, Tc + h, 1.0)[1] - o.dedx_parts(ptype, 0, T, Tc - h, 1.0)[1]) / (2 * h)
+            g = T / ME + 1
+            b2 = 1 - 1 / g ** 2
+            pref = 2 * math.pi * RE ** 2 / (g - 1) / (b2 if model == W_M.MOLLER else 1.0)
+            want = nel * Tc / T * pref * o.dcs(model, T, Tc / T)
+            assert abs(d / want - 1.0) < 1e-6
+
+
+@pytest.mark.parametrize("ptype,model,emax", [(W.ELECTRON, W_M.MOLLER, 0.5),
+                                              (W.POSITRON, W_M.BHABHA, 1.0)])
+def test_delta_ray_total_is_dcs_quadrature(oracle_mod, ptype, model, emax):
+    o = oracle_mod.Oracle(W.pbps_electrons(1))
+    Tc = o.wl.e_cut
+    nel = o.n_el(0)
+    for T in [3.0, 30.0, 3e3]:
+        g = T / ME + 1
+        b2 = 1 - 1 / g ** 2
+        pref = 2 * math.pi * RE ** 2 / (g - 1) / (b2 if model == W_M.MOLLER else 1.0)
+        val, _ = integrate.quad(lambda e: o.dcs(model, T, e), Tc / T, emax, epsrel=1e-12, limit=200)
+        assert abs(o.xs(ptype, 1, 0, T) / (nel * pref * val) - 1.0) < 1e-9
+
+
+# ----------------------------------------------------------------------------- annihilation
+def test_annihilation_total_is_heitler_dcs_quadrature(oracle_mod):
+    o = oracle_mod.Oracle(W.pbps_electrons(1))
+    nel = o.n_el(0)
+    for T in [0.01, 0.5, 10.0, 1e3, 1e5]:
+        g = T / ME + 1
+        s = math.sqrt((g - 1) / (g + 1))
+        a, b = 0.5 * (1 - s), 0.5 * (1 + s)
+        val, _ = integrate.quad(lambda e: o.dcs(W_M.ANNIH, T, e), a, b, epsrel=1e-12, limit=400,
+                                points=[0.5])
+        tot = math.pi * RE ** 2 / (2 * (g + 1) * (g * g - 1)) * val
+        assert abs(o.xs(W.POSITRON, 2, 0, T) / nel / tot - 1.0) < 1e-8
+
+
+# ----------------------------------------------------------------------------- kinematics
+def _rand_dir(rng):
+    c = rng.uniform(-1, 1)
+    p = rng.uniform(0, 2 * math.pi)
+    s = math.sqrt(1 - c * c)
+    return np.array([s * math.cos(p), s * math.sin(p), c])
+
+
+def _kids(out):
+    n = int(out[5])
+    return [(int(out[6 + 5 * j]), out[7 + 5 * j], out[8 + 5 * j:11 + 5 * j]) for j in range(n)]
+
+
+def test_compton_kinematics_conserve_four_momentum(oracle_mod):
+    wl = dataclasses.replace(W.pbps_electrons(1), e_cut=1e-3, gamma_cut=1e-3)
+    o = oracle_mod.Oracle(wl)
+    rng = np.random.default_rng(1)
+    for _ in range(300):
+        k = 10 ** rng.uniform(-2, 4)
+        d = _rand_dir(rng)
+        u = rng.uniform(1e-7, 1, 8)
+        r, out = o.interact(W.GAMMA, 0, k, d, u)
+        kids = _kids(out)
+        k1 = out[0] if r == 1 else 0.0
+        Te = kids[0][1] if kids else 0.0
+        assert abs(k1 + Te + out[4] - k) < 1e-12 * k
+        if r == 1 and kids:
+            pe = math.sqrt(Te * (Te + 2 * ME))
+            p = k * d - k1 * out[1:4]
+            assert abs(np.linalg.norm(p) - pe) < 1e-9 * k
+            assert np.allclose(p / np.linalg.norm(p), kids[0][2], atol=1e-9)
+
+
+@pytest.mark.parametrize("ptype", [W.ELECTRON, W.POSITRON])
+def test_delta_ray_kinematics_conserve_four_momentum(oracle_mod, ptype):
+    o = oracle_mod.Oracle(W.pbps_electrons(1))
+    rng = np.random.default_rng(2)
+    for _ in range(300):
+        T = 10 ** rng.uniform(0.5, 5)
+        d = _rand_dir(rng)
+        u = rng.uniform(1e-7, 1, 8)
+        r, out = o.interact(ptype, 1, T, d, u)
+        if r < 0:
+            continue
+        (kt, Td, dd), = _kids(out)[:1]
+        assert kt == W.ELECTRON
+        Tp = out[0] if r == 1 else 0.0
+        assert abs(Tp + Td + out[4] - T) < 1e-12 * T
+        if r == 1:
+            P = math.sqrt(T * (T + 2 * ME))
+            pd = math.sqrt(Td * (Td + 2 * ME))
+            pp = P * d - pd * np.asarray(dd)
+            assert abs(np.linalg.norm(pp) - math.sqrt(Tp * (Tp + 2 * ME))) < 1e-8 * P
+
+
+def test_annihilation_in_flight_conserves_four_momentum(oracle_mod):
+    o = oracle_mod.Oracle(W.pbps_electrons(1))
+    rng = np.random.default_rng(3)
+    for _ in range(300):
+        T = 10 ** rng.uniform(-2, 5)
+        d = _rand_dir(rng)
+        r, out = o.interact(W.POSITRON, 2, T, d, rng.uniform(1e-7, 1, 8))
+        (t1, k1, d1), (t2, k2, d2) = _kids(out)
+        assert r == 0 and t1 == t2 == W.GAMMA
+        assert abs(k1 + k2 - (T + 2 * ME)) < 1e-12 * (T + 2 * ME)
+        P = math.sqrt(T * (T + 2 * ME))
+        assert np.allclose(P * d, k1 * np.asarray(d1) + k2 * np.asarray(d2), atol=1e-8 * (T + ME))
+
+
+def test_pair_and_brems_conserve_energy(oracle_mod):
+    wl = dataclasses.replace(W.pbps_electrons(1), e_cut=1e-3, gamma_cut=1e-3)
+    o = oracle_mod.Oracle(wl)
+    rng = np.random.default_rng(4)
+    for _ in range(200):
+        k = 10 ** rng.uniform(0.1, 5)
+        r, out = o.interact(W.GAMMA, 2, k, _rand_dir(rng), rng.uniform(1e-7, 1, 8))
+        if r < 0:
+            continue
+        s = sum(e for (_, e, _) in _kids(out)) + out[4]
+        assert abs(s + 2 * ME - k) < 1e-11 * k
+        T = 10 ** rng.uniform(0, 5)
+        r, out = o.interact(W.ELECTRON, 0, T, _rand_dir(rng), rng.uniform(1e-7, 1, 8))
+        if r < 0:
+            continue
+        s = sum(e for (_, e, _) in _kids(out)) + out[4] + (out[0] if r == 1 else 0.0)
+        assert abs(s - T) < 1e-11 * T
+
+
+# ----------------------------------------------------------------------------- alias samplers
+MODELS = {
+    W_M.COMPTON: ("gamma", lambda E, c: (1.0 / (1.0 + 2.0 * E / ME), 1.0), "log"),
+    W_M.PAIR: ("gamma", lambda E, c: (ME / E, 1.0 - ME / E), "lin"),
+    W_M.BREM: ("e", lambda E, c: (c, E), "log"),
+    W_M.MOLLER: ("e", lambda E, c: (c / E, 0.5), "log"),
+    W_M.BHABHA: ("e", lambda E, c: (c / E, 1.0), "log"),
+    W_M.ANNIH: ("e", lambda E, c: (0.5 * (1 - math.sqrt((E / ME) / (E / ME + 2))), 0.5), "log"),
+}
+
+
+def _edges(lo, hi, kind, n):
+    t = np.linspace(0, 1, n + 1)
+    if kind == "lin":
+        return lo + t * (hi - lo)
+    if kind == "log":
+        return lo * (hi / lo) ** t
+    return 1.0 / (1.0 / lo - t * (1.0 / lo - 1.0 / hi))
+
+
+@pytest.mark.parametrize("model", sorted(MODELS))
+def test_alias_sampler_matches_dcs_chi_square(oracle_mod, model):
+    """At the grid energies of the sampling tables, samples follow the exact DCS."""
+    o = oracle_mod.Oracle(W.pbps_electrons(1))
+    cut = {W_M.BREM: o.wl.gamma_cut, W_M.MOLLER: o.wl.e_cut, W_M.BHABHA: o.wl.e_cut}.get(model, 0.0)
+    E_lo, nE = o.alias_info(model)
+    rng = np.random.default_rng(100 + model)
+    _, lim, kind = MODELS[model]
+    for ie in [1, nE // 2, nE - 1]:
+        E = E_lo * 10 ** (ie / 8)
+        lo, hi = lim(E, cut)
+        n = 100_000
+        u = rng.integers(1, 2 ** 24 + 1, size=(n, 3)) / 2.0 ** 24
+        u[:, 0] = 0.5  # grid choice irrelevant exactly on a node
+        v, _ = o.alias_sample(model, np.full(n, E), u)
+        assert v.min() >= lo * (1 - 1e-9) and v.max() <= hi * (1 + 1e-9)
+        edges = _edges(lo, hi, kind, 40)
+        if kind == "log":  # integrate v * dcs(v) over ln v
+            f = lambda t: math.exp(t) * o.dcs(model, E, math.exp(t), cut)  # noqa: E731
+            lims = np.log(edges)
+        else:
+            f = lambda x: o.dcs(model, E, x, cut)  # noqa: E731
+            lims = edges
+        pb = np.array([integrate.quad(f, a, b, epsrel=1e-11, epsabs=0)[0]
+                       for a, b in zip(lims[:-1], lims[1:])])
+        pb /= pb.sum()
+        h, _ = np.histogram(v, bins=edges)
+        exp = pb * n
+        ok = exp > 20
+        chi2 = ((h[ok] - exp[ok]) ** 2 / exp[ok]).sum()
+        p = stats.chi2.sf(chi2, ok.sum() - 1)
+        assert p > 1e-3, (model, E, chi2, ok.sum(), p)
+
+
+# ----------------------------------------------------------------------------- tables / range
+def test_table_interpolation_within_bound(oracle_mod):
+    """Linear-in-lnE interpolation of the node values stays within the stated
+    bounds of the exact quantity at the midpoints between nodes."""
+    o = oracle_mod.Oracle(W.pbps_electrons(1))
+    g = o.grid()
+    mids = np.sqrt(g[:-1] * g[1:])
+    bounds = {(W.GAMMA, 0): 2e-3, (W.GAMMA, 1): 1e-2, (W.GAMMA, 2): 2e-2,
+              (W.ELECTRON, 0): 2e-2, (W.ELECTRON, 1): 2e-2, (W.POSITRON, 2): 2e-3}
+    for (t, q), b in bounds.items():
+        for m in (0, 1):
+            ex = np.array([o.xs(t, q, m, e) for e in mids])
+            it = o.lookup(t, q, m, mids)
+            sel = ex > 0
+            # near thresholds the relative error is unbounded: skip the first 4 nonzero nodes
+            idx = np.nonzero(sel)[0][4:]
+            rel = np.abs(it[idx] / ex[idx] - 1)
+            assert rel.max() < b, (t, q, m, rel.max())
+
+
+def test_range_derivative_is_inverse_stopping_power(oracle_mod):
+    o = oracle_mod.Oracle(W.pbps_electrons(1))
+    for t in (W.ELECTRON, W.POSITRON):
+        for E in [0.003, 0.05, 0.7, 3.0, 40.0, 900.0]:
+            h = 1e-5
+            dR = (o.range_exact(t, 0, E * (1 + h)) - o.range_exact(t, 0, E * (1 - h))) / (2 * E * h)
+            assert abs(dR * o.dedx(t, 0, E) - 1.0) < 1e-6
+
+
+def test_range_inverse_round_trip(oracle_mod):
+    """Continuous loss over s = R(E) - R(E') returns E' (exact inverse of the
+    interpolated range) whenever the step is not in the linear-loss regime."""
+    o = oracle_mod.Oracle(W.pbps_electrons(1))
+    rng = np.random.default_rng(5)
+    for t in (W.ELECTRON, W.POSITRON):
+        qR = 2 if t == W.ELECTRON else 3
+        for _ in range(200):
+            E = 10 ** rng.uniform(-2.5, 5)
+            Ep = E * rng.uniform(0.002, 0.95)
+            Ep = max(Ep, 1.5e-3)
+            s = o.lookup(t, qR, 0, E)[0] - o.lookup(t, qR, 0, Ep)[0]
+            if s <= 0.01 * o.lookup(t, qR, 0, E)[0]:
+                continue
+            got = o.eloss(t, 0, E, s)[0]
+            assert abs(got / Ep - 1) < 1e-9
+
+
+# ----------------------------------------------------------------------------- navigator
+def _inside(pos, zlo, zhi, hx, hy):
+    return zlo <= pos[2] <= zhi and -hx <= pos[0] <= hx and -hy <= pos[1] <= hy
+
+
+def test_distance_matches_bruteforce_bisection(oracle_mod):
+    """Distance to the sub-slab boundary equals the exit point found by
+    bisection on exact rational membership tests."""
+    o = oracle_mod.Oracle(W.pbps_electrons(1))
+    rng = np.random.default_rng(6)
+    hx = hy = Fraction(20)
+    for _ in range(60):
+        sub = int(rng.integers(0, o.n_subtotal()))
+        zlo, zhi = o.plane_z(sub), o.plane_z(sub + 1)
+        pos = np.array([rng.uniform(-19.9, 19.9), rng.uniform(-19.9, 19.9), rng.uniform(zlo, zhi)])
+        d = _rand_dir(rng)
+        s, nxt, pl = o.distance(pos, d, sub)
+        P = [Fraction(float(x)) for x in pos]
+        D = [Fraction(float(x)) for x in d]
+        lo, hi = Fraction(0), Fraction(100)
+        Z0, Z1 = Fraction(zlo), Fraction(zhi)
+        for _ in range(70):
+            mid = (lo + hi) / 2
+            if _inside([P[i] + mid * D[i] for i in range(3)], Z0, Z1, hx, hy):
+                lo = mid
+            else:
+                hi = mid
+        assert abs(s - float(lo)) < 1e-9 * max(1.0, s)
+        if pl >= 0:
+            assert nxt in (sub - 1, sub + 1, -1)
+        else:
+            assert nxt == -1
+
+
+# ----------------------------------------------------------------------------- transport
+def test_unscattered_transmission_is_exp_minus_mu_x(oracle_mod):
+    """1 MeV photons through 10 cm water-like: P(no interaction) = exp(-mu x)."""
+    wl = W.photon_slab(100_000)
+    o = oracle_mod.Oracle(wl)
+    mu = o.xs(W.GAMMA, 0, 0, 1.0) + o.xs(W.GAMMA, 1, 0, 1.0)
+    T = math.exp(-mu * 10.0)
+    assert abs(T - 0.49359) < 2e-5
+    r = o.transport(n_threads=4)
+    f = r["counts"][:, 10].mean()
+    sig = math.sqrt(T * (1 - T) / wl.n_events)
+    assert abs(f - T) < 3 * sig
+
+
+def _conservation(wl, res):
+    c = res["counts"]
+    T0 = np.zeros(wl.n_events)
+    np.add.at(T0, wl.primaries["event"], wl.primaries["E"])
+    npos = np.zeros(wl.n_events)
+    np.add.at(npos, wl.primaries["event"], (wl.primaries["type"] == W.POSITRON).astype(float))
+    tot = res["edep"].sum(1) + res["escape"]
+    resid = (tot - (T0 + 2 * ME * (c[:, 8] - c[:, 7]))) / T0
+    charge = (c[:, 7] + npos) - (c[:, 8] + c[:, 9])
+    return resid, charge
+
+
+@pytest.mark.parametrize("make", [lambda: W.pbps_electrons(20, 1000.0),
+                                  lambda: W.pbps_mixed(30).subset(30),
+                                  lambda: W.wsi_cells(3, 5000.0),
+                                  lambda: W.pblar_testem3(5, 2000.0)])
+def test_energy_and_charge_conservation_per_event(oracle_mod, make):
+    wl = make()
+    if wl.name.startswith("mixed"):
+        wl.primaries["E"] = np.minimum(wl.primaries["E"], 3000.0)
+    o = oracle_mod.Oracle(wl)
+    res = o.transport(n_threads=4)
+    resid, charge = _conservation(wl, res)
+    assert np.abs(resid).max() < 1e-9
+    assert np.all(charge == 0)
+    if "cell" in res:
+        assert abs(res["cell"].sum() - res["edep"].sum()) < 1e-9 * res["edep"].sum()
+
+
+def test_transport_independent_of_thread_count(oracle_mod):
+    wl = W.pbps_electrons(12, 2000.0)
+    o = oracle_mod.Oracle(wl)
+    a = o.transport(n_threads=1)
+    b = o.transport(n_threads=5)
+    assert np.array_equal(a["counts"], b["counts"])
+    assert np.array_equal(a["edep"], b["edep"])
+
+
+def test_shower_profile_sanity(oracle_mod):
+    """10 GeV e- in 50 x (Pb 2 mm + PS 5 mm) (18 X0): nearly contained, with the
+    maximum a few radiation lengths deep."""
+    wl = W.pbps_electrons(10, 10_000.0)
+    o = oracle_mod.Oracle(wl)
+    r = o.transport(n_threads=4)
+    per_layer = r["edep"].reshape(10, 50, 2).sum(2).mean(0)
+    assert per_layer.sum() / 10_000.0 > 0.95
+    assert 3 <= int(np.argmax(per_layer)) <= 14

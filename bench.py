@@ -1,0 +1,290 @@
+"""Benchmark: 10 GeV e- showers/s (and EM steps/s) on the 50-layer Pb/polystyrene
+calorimeter, 2000 events per step, through the libgv C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One step = one gv_transport call over the whole batch (every stage of the
+stepping loop for every track of every event).  `value` times it with inputs
+and tallies resident in HBM; `e2e` times the same call with host buffers
+(host->device primaries and device->host tallies inside the timed region).
+Between timed steps L2 is flushed by writing a 512 MiB buffer.  Under torchrun
+each rank transports its own 2000-event shard (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build)
+on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2005_00949_gb300 import workloads as W  # noqa: E402
+
+METRIC = "EM steps/s and 10 GeV e- showers/s on 1 GB300; HBM roofline fraction"
+N_EVENTS = 2000
+E0 = 10_000.0
+# algorithmic DRAM bytes of one track step in a step-synchronous wavefront:
+# read + write the 64 B mixed-precision track record, plus 64 B per secondary
+TRACK_BYTES = 64
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _workload(rank: int):
+    wl = W.pbps_electrons(N_EVENTS, E0)
+    # each rank owns a distinct event range (distinct Philox streams)
+    wl.seed = W.DEFAULT_SEED + rank
+    return wl
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.p is None:
+            return
+        time.sleep(0.25)
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def cpu_baseline(wl, budget_events: int | None = None):
+    """The FP64 oracle, as it stands, on the host cores over a bounded sample."""
+    import oracle
+    nthr = os.cpu_count() or 1
+    n = budget_events or max(nthr, 16 * nthr)
+    sub = wl.subset(min(n, wl.n_events))
+    o = oracle.Oracle(sub)
+    t = time.perf_counter()
+    r = o.transport(n_threads=nthr)
+    dt = time.perf_counter() - t
+    steps = int(r["counts"][:, 0].sum())
+    return {"value": sub.n_events / dt, "unit": "showers/s", "cores": nthr, "kind": "oracle",
+            "sample": f"{sub.n_events} x 10 GeV e- of the 2000-event workload, {nthr} threads, "
+                      f"{dt:.2f} s wall",
+            "steps_per_s": steps / dt}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = _workload(0)
+    nthr = os.cpu_count() or 1
+    n_ev = 8 * nthr
+    for _ in range(args.warmup):
+        cpu_baseline(wl, nthr)
+    times, vals = [], []
+    for _ in range(args.steps):
+        b = cpu_baseline(wl, n_ev)
+        vals.append(b["value"])
+        times.append(n_ev / b["value"])
+    v = n_ev * len(times) / sum(times)
+    line = {"metric": METRIC, "value": v, "unit": "showers/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * sum(times) / len(times) * (N_EVENTS / n_ev),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "pbps50_e-10GeV_2000ev (config 4)", "events_per_step": N_EVENTS,
+                       "sample_events_per_step": n_ev, "parallelism": "host threads"},
+            "cpu_baseline": {"value": v, "unit": "showers/s", "cores": nthr, "kind": "oracle",
+                             "sample": f"{n_ev} events per step of the 2000-event workload"},
+            "e2e": {"value": v, "unit": "showers/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gv")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2005_00949_gb300 import gv
+
+    wl = _workload(rank)
+    ctx = gv.Context(wl, gv.gv_default_config(stack_capacity=1 << 23))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    prim_d = torch.from_numpy(wl.primaries.view(np.uint8).copy()).to(dev)
+    nsub = ctx.n_subtotal
+    edep = torch.zeros((wl.n_events, nsub), dtype=torch.float64, device=dev)
+    esc = torch.zeros(wl.n_events, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        return ctx.gv_transport(prim_d, wl.n_events, wl.seed, edep, None, esc, None, stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # ---- device-resident timing
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    steps_tot, kernel_ms, launches, sec = 0, 0.0, 0, 0
+    barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)
+            starts[i].record(stream)
+            res = step()
+            ends[i].record(stream)
+            steps_tot += res.counters[0]
+            sec += res.counters[4] + res.counters[5] + res.counters[6] - wl.n_events
+            kernel_ms += res.kernel_ms
+            launches += ctx.lib.gv_last_launches(ctx.h)
+        torch.cuda.synchronize()
+    barrier()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    events_all = wl.n_events * world
+    value = events_all / (ms_per_step / 1000.0)
+    steps_per_s = steps_tot * world / (ms / 1000.0)
+    # ---- end to end through the C ABI with host buffers
+    prim_h = torch.from_numpy(wl.primaries.view(np.uint8).copy()).pin_memory()
+    edep_h = torch.zeros((wl.n_events, nsub), dtype=torch.float64).pin_memory()
+    esc_h = torch.zeros(wl.n_events, dtype=torch.float64).pin_memory()
+    e_ms = 0.0
+    n_e2e = max(1, min(args.steps, 5))
+    barrier()
+    torch.cuda.synchronize()
+    for i in range(n_e2e):
+        flush.fill_(i & 0xff)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ctx.gv_transport(prim_h, wl.n_events, wl.seed, edep_h, None, esc_h, None, stream)
+        torch.cuda.synchronize()
+        e_ms += (time.perf_counter() - t) * 1000.0
+    if dist is not None:
+        t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_ms = float(t.item())
+    e2e = events_all / (e_ms / n_e2e / 1000.0)
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+    # ---- roofline of the step kernel
+    peak, peak_kind = _peaks()
+    sec_per_step = sec / max(steps_tot, 1)
+    alg_bytes = steps_tot / world * (2 * TRACK_BYTES + TRACK_BYTES * sec_per_step)
+    achieved = alg_bytes / (kernel_ms / 1000.0) / 1e9 if kernel_ms > 0 else None
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get("dram_bytes_per_step_mixed")
+            if traffic is not None:
+                traffic = traffic * steps_tot / args.steps / max(launches / args.steps, 1)
+    except Exception:
+        traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": "showers/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "pbps50_e-10GeV_2000ev (config 4): 2000 x 10 GeV e- on "
+                               "50 x (2 mm Pb + 5 mm polystyrene), 40x40 cm, cuts 1 MeV",
+                   "events_per_gpu": wl.n_events, "precision": "mixed FP32 physics / FP64 positions",
+                   "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"events x{world}"},
+        "steps_per_s": steps_per_s,
+        "track_steps_per_step": steps_tot / args.steps / 1.0,
+        "kernel_ms_per_step": kernel_ms / args.steps,
+        "gpu_launches": int(launches),
+        "e2e": {"value": e2e, "unit": "showers/s",
+                "h2d_bytes_per_step": int(wl.primaries.nbytes),
+                "d2h_bytes_per_step": int(edep_h.numel() * 8 + esc_h.numel() * 8)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "kernel": "gv::step_kernel<float>",
+                     "alg_bytes_per_step": 2 * TRACK_BYTES + TRACK_BYTES * sec_per_step},
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(line))
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,217 @@
+/*
+ * gv.h -- C ABI of the GB300 (sm_103a) electromagnetic shower transport
+ * library libgv.so: the per-track stepping loop of GeantV (arXiv:2005.00949,
+ * Sec. 2.1.2 "Scalar and vector workflows", Fig. "simulation stages"), run for
+ * thousands of events at once on one GPU.
+ *
+ * Conventions
+ *  - Every call returns GV_OK (0) or a negative GV_ERR_* code; nothing throws
+ *    across the ABI, nothing aborts the process, no kernel traps.
+ *  - Energies in MeV (kinetic), lengths in cm, densities in g/cm3.
+ *  - Particle types: 0 gamma, 1 electron, 2 positron.
+ *  - A gv_ctx owns every device allocation it makes (tables, track queues,
+ *    tallies); the caller owns primaries and result buffers.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream), e.g. torch.cuda.current_stream().cuda_stream.
+ *  - Pointers documented "host or device" may be either: the library asks the
+ *    CUDA driver which one it got (unified addressing).
+ */
+#ifndef GV_H
+#define GV_H
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GV_OK 0
+#define GV_ERR_BAD_ARG -1    /* an argument is out of range or inconsistent */
+#define GV_ERR_NO_TABLES -2  /* gv_build_tables has not run */
+#define GV_ERR_OOM -3        /* a device allocation failed */
+#define GV_ERR_STACK_FULL -4 /* a track queue overflowed its capacity */
+#define GV_ERR_TIMEOUT -5    /* generation budget exhausted before all tracks ended */
+#define GV_ERR_NUMERIC -6    /* a track reached a non-finite energy or position */
+#define GV_ERR_CUDA -7       /* a CUDA runtime call failed */
+
+#define GV_MAX_ELEM 4
+#define GV_MAX_MAT 4
+#define GV_MAX_SUB 8
+#define GV_MAX_SUBTOTAL 1024
+#define GV_NCOUNT 12
+
+/* process bits of gv_cuts.process_mask */
+#define GV_P_COMPTON (1u << 0)
+#define GV_P_PHOTO (1u << 1)
+#define GV_P_PAIR (1u << 2)
+#define GV_P_BREM (1u << 3)
+#define GV_P_IONI (1u << 4)
+#define GV_P_ANNIH (1u << 5)
+
+/* arithmetic of the stepping loop */
+#define GV_MIXED 0 /* FP32 physics, tables and energies; FP64 positions and boundaries */
+#define GV_FP64 1  /* FP64 everywhere */
+
+/* scheduling */
+#define GV_BATCHED 0               /* all events share one population of tracks */
+#define GV_ONE_EVENT_PER_LAUNCH 1  /* plain comparator: one event in flight at a time */
+
+/* indices of gv_result.counters and of the per-event counter rows */
+enum {
+  GV_C_STEPS = 0, GV_C_STEPS_G, GV_C_STEPS_EM, GV_C_STEPS_EP,
+  GV_C_TRK_G, GV_C_TRK_EM, GV_C_TRK_EP, GV_C_PAIR, GV_C_ANNIH,
+  GV_C_EP_ESC, GV_C_UNSCAT, GV_C_GENERATIONS
+};
+
+/* A material: n_elem elements with atomic number Z, atomic mass A (g/mol) and
+ * mass fraction w; density rho (g/cm3); mean excitation energy I (eV). */
+typedef struct {
+  int n_elem;
+  double Z[GV_MAX_ELEM], A[GV_MAX_ELEM], w[GV_MAX_ELEM];
+  double rho;
+  double I_eV;
+} gv_material;
+
+/* Layered box along +z from z = 0: n_layers repetitions of n_sub sub-slabs
+ * (thickness sub_thick_cm[j], material sub_mat[j]).  Transverse half widths
+ * half_x_cm/half_y_cm (<= 0: unbounded).  nx_cells x ny_cells scoring cells per
+ * layer over the full transverse extent (0: no cell scoring). */
+typedef struct {
+  int n_layers;
+  int n_sub;
+  double sub_thick_cm[GV_MAX_SUB];
+  int sub_mat[GV_MAX_SUB];
+  double half_x_cm, half_y_cm;
+  int nx_cells, ny_cells;
+} gv_layers;
+
+/* Production cuts (MeV): gamma_cut splits bremsstrahlung into continuous and
+ * discrete parts, e_cut splits ionisation and decides whether Compton,
+ * photo- and pair-produced leptons are tracked; track_cut (>= 1 keV) ends
+ * tracks.  process_mask: GV_P_* bits of the enabled discrete processes. */
+typedef struct {
+  double gamma_cut_MeV, e_cut_MeV, track_cut_MeV;
+  unsigned process_mask;
+} gv_cuts;
+
+/* Launch and memory configuration; gv_default_config fills every field. */
+typedef struct {
+  int precision;              /* GV_MIXED or GV_FP64 */
+  int mode;                   /* GV_BATCHED or GV_ONE_EVENT_PER_LAUNCH */
+  int block_size;             /* threads per block: 64..512, multiple of 32 */
+  int blocks_per_sm;          /* persistent blocks per SM */
+  int steps_per_claim;        /* steps a thread takes on a claimed track per generation */
+  int tail_steps_per_claim;   /* the same when fewer than tail_threshold tracks are live */
+  long long tail_threshold;
+  long long stack_capacity;   /* tracks per particle-type queue (each double-buffered) */
+  long long refill_low_water; /* inject primaries while fewer live tracks than this */
+  long long refill_batch;     /* at most this many primaries per generation */
+  int generations_per_graph;  /* generations captured in one CUDA graph (even) */
+  long long max_generations;  /* budget; exceeded -> GV_ERR_TIMEOUT */
+  int per_event_counts;       /* 1: keep GV_NCOUNT counters per event (slower) */
+  int process_sort;           /* 1: re-basket interacting tracks by process in each block */
+} gv_config;
+
+/* A primary track; layout shared with the seeded input generator. */
+typedef struct {
+  int type;
+  double E_MeV;
+  double x, y, z;   /* must lie inside the box (z in [0, Z_total]) */
+  double u, v, w;   /* unit direction */
+  unsigned event;   /* event index, < n_events */
+} gv_primary;
+
+/* Results of one gv_transport call.  Buffers are caller-owned, host or device,
+ * zeroed by the library before it accumulates into them:
+ *   edep         [n_events][n_layers*n_sub]  energy deposit per sub-slab (MeV)
+ *   cell_edep    [n_layers][nx][ny] or NULL   summed over events (MeV)
+ *   escape_E     [n_events] or NULL            kinetic energy leaving the box
+ *   event_counts [n_events][GV_NCOUNT] or NULL (requires per_event_counts)
+ * counters[], status and kernel_ms are filled on return. */
+typedef struct {
+  double *edep;
+  double *cell_edep;
+  double *escape_E;
+  long long *event_counts;
+  unsigned long long counters[16];
+  int status;
+  double kernel_ms;   /* device time of the step-kernel graphs (CUDA events on the work stream) */
+} gv_result;
+
+/* Fill *cfg with defaults (batched, mixed precision, autotuned launch shape). */
+int gv_default_config(gv_config *cfg);
+
+/* Create a context: validates the materials (n_mats <= GV_MAX_MAT), geometry
+ * (n_layers*n_sub <= GV_MAX_SUBTOTAL) and cuts, allocates the device queues.
+ * cfg = NULL selects defaults.  Uses the current CUDA device. */
+int gv_setup(void **ctx_out, const gv_material *mats, int n_mats, const gv_layers *geo,
+             const gv_cuts *cuts, const gv_config *cfg);
+
+/* Build the cross-section, range and alias sampling tables in FP64 on the host
+ * (ComputeIntLen tables of Sec. 2.1.2, "sampling tables" of Sec. 3.5) and
+ * upload them in the context's precision.  Synchronous. */
+int gv_build_tables(void *ctx);
+
+/* Transport n primaries (host or device array) of n_events events with the
+ * given seed, on `stream`.  Runs the stepping loop (Sec. 2.1.2 stages, stack
+ * of Sec. 2.1.2, scoring of Sec. 3.8.1) until every track has ended and
+ * copies the tallies into res.  Blocks the calling thread until done. */
+int gv_transport(void *ctx, const gv_primary *p, long long n, long long n_events,
+                 unsigned long long seed, void *stream, gv_result *res);
+
+/* Wait for all work of the context on `stream`; returns the last status. */
+int gv_sync(void *ctx, void *stream);
+
+/* Release every resource of the context. */
+void gv_destroy(void *ctx);
+
+/* Static description of an error code. */
+const char *gv_strerror(int code);
+
+/* Number of kernel launches the last gv_transport issued. */
+long long gv_last_launches(void *ctx);
+
+/* ---- element-wise entry points (device pointers, asynchronous on stream) ----
+ * They run the same device functions as gv_transport, in the context's
+ * precision, one element per thread; inputs and outputs are FP64 arrays. */
+
+/* Philox4x32-10 (Random123 family, Sec. 3.3.2): out[4i..4i+3] from counter
+ * ctr[4i..4i+3] and key key[2i..2i+1]. */
+int gv_unit_philox(const unsigned *ctr, const unsigned *key, unsigned *out, long long n,
+                   void *stream);
+
+/* Table lookup (ComputeIntLen, Spline::GetValueAt of Sec. 6.6) of particle
+ * `type` in material `mat` at energies E[i]: out[4i..4i+3] = the four
+ * interpolated table quantities (gamma: Compton, photo, pair, 0; e-: brems,
+ * ionisation, range, 0; e+: brems, ionisation, annihilation, range). */
+int gv_unit_xs_lookup(void *ctx, int type, int mat, const double *E, long long n, double *out,
+                      void *stream);
+
+/* Continuous loss (AlongStepAction): post-step kinetic energy after a step
+ * s[i] from E[i]. */
+int gv_unit_eloss(void *ctx, int type, int mat, const double *E, const double *s, long long n,
+                  double *out, void *stream);
+
+/* Alias-table sampling (Sec. 3.5) of model m (0 Compton, 1 pair, 2 brems,
+ * 3 Moller, 4 Bhabha, 5 annihilation) at E[i] with uniforms u[3i..3i+2]
+ * (grid choice, bin, in-bin): out[2i] = physical variable, out[2i+1] = xi. */
+int gv_unit_alias_sample(void *ctx, int model, const double *E, const double *u, long long n,
+                         double *out, void *stream);
+
+/* Final state of process `proc` for particle `type` at E[i], direction
+ * dir[3i..], uniforms u[8i..8i+7]: out[24i..] = {E' (-1 if the primary
+ * ended), dir'[3], local deposit, n_children, then per child: type, E, dir[3]};
+ * ret[i] = 1 survived, 0 ended, -1 no interaction possible. */
+int gv_unit_interact(void *ctx, int type, int proc, const double *E, const double *dir,
+                     const double *u, long long n, double *out, int *ret, void *stream);
+
+/* Distance to the boundary of sub-slab sub[i] (GeomQuery, Box::DistanceToIn
+ * of Sec. 3.2) from pos[3i..] along dir[3i..]; next[i] = sub-slab entered
+ * (-1 = leaves the box), plane[i] = crossed z-plane index or -2/-3 for the
+ * x/y walls. */
+int gv_unit_distance(void *ctx, const double *pos, const double *dir, const int *sub,
+                     long long n, double *dist, int *next, int *plane, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -43,7 +43,6 @@
 /* charged-particle step limit and continuous-loss constants */
 #define STEP_ALPHA_R 0.2
 #define STEP_RHO_F 0.1
-#define LINLOSS_FRAC 0.01
 
 #define TAG_ID 0x80000000u
 
@@ -611,7 +610,9 @@ double or_table_lookup(const or_ctx *c, int type, int q, int mat, double E) {
   return v[i] + f * (v[i + 1] - v[i]);
 }
 
-/* continuous loss along a step s from kinetic energy E (charged types) */
+/* Continuous loss along a step s from kinetic energy E (charged types): the
+ * post-step energy is the exact inverse of the interpolated range,
+ * E' = R^-1(R(E) - s), with R piecewise linear in ln E between nodes. */
 double or_eloss(const or_ctx *c, int type, int mat, double E, double s) {
   int qR = type == OR_ELECTRON ? 2 : 3;
   const double *R = c->tab[type][qR][mat];
@@ -620,11 +621,6 @@ double or_eloss(const or_ctx *c, int type, int mat, double E, double s) {
   grid_pos(E, &i, &f);
   double Rv = R[i] + f * (R[i + 1] - R[i]);
   if (s >= Rv) return 0.0;
-  if (s <= LINLOSS_FRAC * Rv) {
-    double S = (log(10.0) / GRID_PPD) * E / (R[i + 1] - R[i]);
-    double Ep = E - s * S;
-    return Ep > 0.0 ? Ep : 0.0;
-  }
   double r = Rv - s;
   if (r < R[0]) return GRID_EMIN * r / R[0];
   int lo = 0, hi = GRID_N - 1; /* find R[lo] <= r < R[lo+1] */

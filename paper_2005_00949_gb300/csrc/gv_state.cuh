@@ -1,0 +1,61 @@
+// gv_state.cuh -- device-resident state of a transport call: the
+// double-buffered per-type track queues (the StackBuffer / stage baskets of
+// GeantV Sec. 2.1.2, as structures of arrays), the generation control block
+// and the tally pointers.
+#pragma once
+#include "gv_device.cuh"
+
+namespace gv {
+
+// Structure-of-arrays queue of one particle type.
+template <typename R> struct Queue {
+  double *x, *y, *z;
+  R *u, *v, *w, *E, *nlam;
+  unsigned long long *id;
+  unsigned *ev, *step;
+  int *sf;  // sub-slab | flags << 16
+};
+
+constexpr int kFlagPrimary = 1;
+constexpr int kFlagInteracted = 2;
+
+template <typename R> constexpr size_t track_bytes() {
+  return 3 * sizeof(double) + 5 * sizeof(R) + sizeof(unsigned long long) + 3 * sizeof(unsigned);
+}
+
+// Generation control block.  The last block of every generation writes the
+// plan of the next one; kernels only read it.
+struct Ctl {
+  unsigned cnt[2][3];        // queue fill per buffer parity and type
+  unsigned prim_next;        // primaries handed out so far
+  unsigned prim_begin, prim_count;
+  unsigned chunk_end[4];     // cumulative chunk counts: gamma, e-, e+, primaries
+  unsigned claim;            // chunk claim counter
+  unsigned blocks_done;
+  int K;                     // steps per claimed track this generation
+  int status;
+  int done;
+  int pad;
+  unsigned long long gen;
+  unsigned long long live_peak;
+  unsigned long long counters[16];
+};
+
+template <typename R> struct DevState {
+  View<R> view;              // global-memory table pointers and constants
+  Queue<R> q[2][3];
+  unsigned long long capacity;
+  Ctl *ctl;
+  const gv_primary *prim;
+  const unsigned *order;     // primary visiting order (one-event mode) or null
+  unsigned n_prim, n_events;
+  double *edep, *cell, *escape;
+  unsigned long long *evcnt;
+  unsigned seed_lo, seed_hi;
+  int block_size, mode, K_bulk, K_tail;
+  unsigned long long tail_threshold, low_water, batch, max_gen;
+  int n_mat;
+  unsigned xs_bytes, zb_bytes;  // staged into shared memory
+};
+
+}  // namespace gv

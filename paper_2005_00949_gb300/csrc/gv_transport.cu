@@ -1,0 +1,1008 @@
+// gv_transport.cu -- the stepping loop of GeantV (Sec. 2.1.2, Fig.
+// "simulation stages") as a persistent, chunk-claiming CUDA kernel driven
+// generation by generation from a captured CUDA graph, plus the C ABI.
+//
+// One generation: every live track of the three per-type queues (and the
+// primaries injected by the refill plan) is claimed in chunks of one block,
+// stepped K times, and written back -- survivors and secondaries appended to
+// the other parity's queues with warp-aggregated atomics (the basketizer of
+// scheduler v3, Sec. 2.1.1).  The last block to finish writes the plan of
+// the next generation: queue chunk ranges, primaries to inject (the event
+// server refill, bounded by a live-track budget) and the steps per claim.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gv_state.cuh"
+
+namespace gv {
+
+// ------------------------------------------------------------------ sinks
+struct BlockCnt {
+  unsigned long long c[16];
+};
+
+template <typename R>
+__device__ __forceinline__ void deposit(const View<R> &V, const DevState<R> *S, unsigned ev, int sub, double px,
+                                        double py, R dE) {
+  if (!(dE != R(0)) || sub < 0) return;
+  atomicAdd(&S->edep[static_cast<size_t>(ev) * V.geo.nsub + sub], static_cast<double>(dE));
+  if (S->cell) {
+    const GeoConst &g = V.geo;
+    const int layer = sub / g.nsub_layer;
+    int ix = static_cast<int>(floor((px + g.hx) / g.pitch_x));
+    int iy = static_cast<int>(floor((py + g.hy) / g.pitch_y));
+    ix = ix < 0 ? 0 : (ix >= g.nx ? g.nx - 1 : ix);
+    iy = iy < 0 ? 0 : (iy >= g.ny ? g.ny - 1 : iy);
+    atomicAdd(&S->cell[(static_cast<size_t>(layer) * g.nx + ix) * g.ny + iy], static_cast<double>(dE));
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void count(const DevState<R> *S, BlockCnt *bc, unsigned ev, int c, unsigned long long n = 1) {
+  atomicAdd(&bc->c[c], n);
+  if (S->evcnt) atomicAdd(&S->evcnt[static_cast<size_t>(ev) * GV_NCOUNT + c], n);
+}
+
+template <typename R> struct Trk {
+  double x, y, z;
+  R u, v, w, E, nlam;
+  unsigned long long id;
+  unsigned ev, step;
+  int sub, flags, type;
+};
+
+__device__ __forceinline__ void set_status(Ctl *ctl, int code) { atomicCAS(&ctl->status, 0, code); }
+
+// ------------------------------------------------------------------ one step
+// Returns 1 if the track is still alive.  Secondaries go to `kids`; kk is
+// the step index whose counter blocks derive the children's ids.
+template <typename R>
+__device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kids<R> &kids, uint32_t &kk,
+                          BlockCnt *bc) {
+  kids.n = 0;
+  const uint32_t k = t.step;
+  kk = k;
+  const uint32_t key0 = S->seed_lo ^ t.ev, key1 = S->seed_hi;
+  const uint32_t idlo = static_cast<uint32_t>(t.id), idhi = static_cast<uint32_t>(t.id >> 32);
+  const uint4 r0 = philox4x32_10(make_uint4(idlo, idhi, k, 0u), key0, key1);
+  const R tcut = static_cast<R>(V.cut.tcut);
+  if (t.E < tcut) {  // PreStep: tracking cut
+    deposit(V, S, t.ev, t.sub, t.x, t.y, t.E);
+    if (t.type == 2) {
+      const uint4 r1 = philox4x32_10(make_uint4(idlo, idhi, k, 1u), key0, key1);
+      at_rest(kids, u24<R>(r1.z), u24<R>(r1.w));
+      count(S, bc, t.ev, GV_C_ANNIH);
+    }
+    return 0;
+  }
+  const int mat = V.smat[t.sub];
+  // ComputeIntLen
+  if (t.nlam <= R(0)) t.nlam = -m_log(u24<R>(r0.x));
+  const V4<R> s4 = lookup(V, mat, t.type, t.E);
+  const R sig0 = s4.x, sig1 = s4.y, sig2 = (t.type == 1) ? R(0) : s4.z;
+  const R Sig = sig0 + sig1 + sig2;
+  const R INF = r_inf<R>();
+  const R s_phys = Sig > R(0) ? t.nlam / Sig : INF;
+  R s_cont = INF;
+  const bool charged = t.type != 0;
+  if (charged) {
+    const R Rr = t.type == 1 ? s4.z : s4.w;
+    const R a = static_cast<R>(kAlphaR) * Rr, b = Rr < static_cast<R>(kRhoF) ? Rr : static_cast<R>(kRhoF);
+    s_cont = a > b ? a : b;
+  }
+  // GeomQuery
+  int next, plane;
+  const R s_geom = distance(V, t.x, t.y, t.z, t.u, t.v, t.w, t.sub, next, plane);
+  R s = s_cont < s_geom ? s_cont : s_geom;
+  s = s_phys < s ? s_phys : s;
+  const int lim = (s_geom == s) ? 0 : (s_phys == s ? 1 : 2);
+  if (!(s < INF)) {
+    atomicAdd(&S->escape[t.ev], static_cast<double>(t.E));
+    if (t.type == 2) count(S, bc, t.ev, GV_C_EP_ESC);
+    return 0;
+  }
+  // Propagation (FP64 positions)
+  const double sd = static_cast<double>(s);
+  const double mx = t.x + 0.5 * sd * static_cast<double>(t.u);
+  const double my = t.y + 0.5 * sd * static_cast<double>(t.v);
+  t.x += sd * static_cast<double>(t.u);
+  t.y += sd * static_cast<double>(t.v);
+  t.z += sd * static_cast<double>(t.w);
+  if (lim == 0) {
+    if (plane >= 0) t.z = V.zb[plane];
+    else if (plane == -2) t.x = t.u > R(0) ? V.geo.hx : -V.geo.hx;
+    else if (plane == -3) t.y = t.v > R(0) ? V.geo.hy : -V.geo.hy;
+  }
+  if (Sig > R(0)) t.nlam = (lim == 1) ? R(0) : t.nlam - s * Sig;
+  t.step = k + 1;
+  count(S, bc, t.ev, GV_C_STEPS);
+  count(S, bc, t.ev, GV_C_STEPS_G + t.type);
+  const int pre_sub = t.sub;
+  // AlongStepAction
+  if (charged) {
+    const R Ep = eloss(V, mat, t.type, t.E, s);
+    deposit(V, S, t.ev, pre_sub, mx, my, t.E - Ep);
+    t.E = Ep;
+    if (t.E < tcut) {
+      deposit(V, S, t.ev, pre_sub, t.x, t.y, t.E);
+      if (t.type == 2) {
+        const uint4 r1 = philox4x32_10(make_uint4(idlo, idhi, k, 1u), key0, key1);
+        at_rest(kids, u24<R>(r1.z), u24<R>(r1.w));
+        count(S, bc, t.ev, GV_C_ANNIH);
+      }
+      return 0;
+    }
+  }
+  if (lim == 0) {
+    if (next < 0) {
+      atomicAdd(&S->escape[t.ev], static_cast<double>(t.E));
+      if (t.type == 2) count(S, bc, t.ev, GV_C_EP_ESC);
+      if ((t.flags & kFlagPrimary) && !(t.flags & kFlagInteracted) && plane == V.geo.nsub)
+        count(S, bc, t.ev, GV_C_UNSCAT);
+      return 0;
+    }
+    t.sub = next;
+    return 1;
+  }
+  if (lim != 1) return 1;
+  // PostStepActions: process choice, then the final state
+  const R target = u24<R>(r0.y) * Sig;
+  int proc = -1;
+  R cum = sig0;
+  if (target < cum) proc = 0;
+  else {
+    cum += sig1;
+    if (target < cum) proc = 1;
+    else {
+      cum += sig2;
+      if (target < cum) proc = 2;
+    }
+  }
+  if (proc < 0) proc = sig2 > R(0) ? 2 : (sig1 > R(0) ? 1 : (sig0 > R(0) ? 0 : -1));
+  t.nlam = R(-1);
+  if (proc < 0) return 1;
+  const uint4 r1 = philox4x32_10(make_uint4(idlo, idhi, k, 1u), key0, key1);
+  R u[8] = {u24<R>(r0.x), u24<R>(r0.y), u24<R>(r0.z), u24<R>(r0.w),
+            u24<R>(r1.x), u24<R>(r1.y), u24<R>(r1.z), u24<R>(r1.w)};
+  R d[3] = {t.u, t.v, t.w};
+  R local;
+  int np = 0, na = 0;
+  const int r = interact(V, t.type, proc, t.E, d, u, kids, local, np, na);
+  if (r < 0) return 1;
+  t.u = d[0];
+  t.v = d[1];
+  t.w = d[2];
+  t.flags |= kFlagInteracted;
+  if (np) count(S, bc, t.ev, GV_C_PAIR, np);
+  if (na) count(S, bc, t.ev, GV_C_ANNIH, na);
+  deposit(V, S, t.ev, t.sub, t.x, t.y, local);
+  return r;
+}
+
+// ------------------------------------------------------------------ queues
+// Warp-aggregated append: each lane contributes c_q records of type q; one
+// atomic per warp and type reserves the slots.  Must be called by all 32
+// lanes of a converged warp.
+__device__ __forceinline__ unsigned warp_reserve(unsigned *counter, unsigned c, unsigned &total) {
+  const int lane = threadIdx.x & 31;
+  unsigned incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  total = __shfl_sync(0xffffffffu, incl, 31);
+  unsigned base = 0;
+  if (lane == 31 && total) base = atomicAdd(counter, total);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  return base + incl - c;
+}
+
+template <typename R>
+__device__ __forceinline__ void store(const Queue<R> &q, unsigned slot, double x, double y, double z, R u, R v, R w,
+                                      R E, R nlam, unsigned long long id, unsigned ev, unsigned step, int sf) {
+  q.x[slot] = x;
+  q.y[slot] = y;
+  q.z[slot] = z;
+  q.u[slot] = u;
+  q.v[slot] = v;
+  q.w[slot] = w;
+  q.E[slot] = E;
+  q.nlam[slot] = nlam;
+  q.id[slot] = id;
+  q.ev[slot] = ev;
+  q.step[slot] = step;
+  q.sf[slot] = sf;
+}
+
+// S9: append the step's secondaries to the output queues.
+template <typename R>
+__device__ void push_kids(const DevState<R> *S, int out, const Trk<R> &t, const Kids<R> &kids, uint32_t kk,
+                          BlockCnt *bc) {
+  const unsigned any = __ballot_sync(0xffffffffu, kids.n > 0);
+  if (!any) return;
+  uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (kids.n > 0) {
+    const uint32_t key0 = S->seed_lo ^ t.ev;
+    const uint4 a = philox4x32_10(make_uint4(static_cast<uint32_t>(t.id), static_cast<uint32_t>(t.id >> 32), kk, kTagId),
+                                  key0, S->seed_hi);
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+    if (kids.n > 2) {
+      const uint4 b = philox4x32_10(
+          make_uint4(static_cast<uint32_t>(t.id), static_cast<uint32_t>(t.id >> 32), kk, kTagId + 1u), key0, S->seed_hi);
+      w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    unsigned c = 0;
+    for (int j = 0; j < kids.n; ++j) c += kids.type[j] == q;
+    if (!__ballot_sync(0xffffffffu, c > 0)) continue;
+    unsigned total;
+    unsigned slot = warp_reserve(&S->ctl->cnt[out][q], c, total);
+    if ((threadIdx.x & 31) == 0 && total) atomicAdd(&bc->c[GV_C_TRK_G + q], static_cast<unsigned long long>(total));
+    if (c == 0) continue;
+    if (slot + c > S->capacity) {
+      set_status(S->ctl, GV_ERR_STACK_FULL);
+      continue;
+    }
+    for (int j = 0; j < kids.n; ++j) {
+      if (kids.type[j] != q) continue;
+      const unsigned long long id = static_cast<unsigned long long>(w[2 * j]) |
+                                    (static_cast<unsigned long long>(w[2 * j + 1]) << 32);
+      store(S->q[out][q], slot, t.x, t.y, t.z, kids.d[j][0], kids.d[j][1], kids.d[j][2], kids.E[j], R(-1), id, t.ev,
+            0u, t.sub);
+      if (S->evcnt) atomicAdd(&S->evcnt[static_cast<size_t>(t.ev) * GV_NCOUNT + GV_C_TRK_G + q], 1ull);
+      ++slot;
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void push_survivor(const DevState<R> *S, int out, const Trk<R> &t, bool alive) {
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const bool mine = alive && t.type == q;
+    if (!__ballot_sync(0xffffffffu, mine)) continue;
+    unsigned total;
+    const unsigned slot = warp_reserve(&S->ctl->cnt[out][q], mine ? 1u : 0u, total);
+    if (!mine) continue;
+    if (slot >= S->capacity) {
+      set_status(S->ctl, GV_ERR_STACK_FULL);
+      continue;
+    }
+    store(S->q[out][q], slot, t.x, t.y, t.z, t.u, t.v, t.w, t.E, t.nlam, t.id, t.ev, t.step,
+          t.sub | (t.flags << 16));
+  }
+}
+
+// ------------------------------------------------------------------ planning
+template <typename R> __device__ void plan_next(const DevState<R> *S, int pn) {
+  Ctl *c = S->ctl;
+  const unsigned n0 = c->cnt[pn][0], n1 = c->cnt[pn][1], n2 = c->cnt[pn][2];
+  const unsigned long long live = static_cast<unsigned long long>(n0) + n1 + n2;
+  const unsigned rem = S->n_prim - c->prim_next;
+  unsigned inj = 0;
+  if (c->status == 0 && rem > 0) {
+    if (S->mode == GV_ONE_EVENT_PER_LAUNCH) {
+      if (live == 0) {
+        const unsigned first = S->order ? S->order[c->prim_next] : c->prim_next;
+        const unsigned ev = S->prim[first].event;
+        while (inj < rem) {
+          const unsigned i = c->prim_next + inj;
+          const unsigned pi = S->order ? S->order[i] : i;
+          if (S->prim[pi].event != ev) break;
+          ++inj;
+        }
+      }
+    } else if (live < S->low_water || live == 0) {
+      inj = rem < S->batch ? rem : static_cast<unsigned>(S->batch);
+    }
+  }
+  c->prim_begin = c->prim_next;
+  c->prim_count = inj;
+  c->prim_next += inj;
+  const unsigned B = static_cast<unsigned>(S->block_size);
+  c->chunk_end[0] = (n0 + B - 1) / B;
+  c->chunk_end[1] = c->chunk_end[0] + (n1 + B - 1) / B;
+  c->chunk_end[2] = c->chunk_end[1] + (n2 + B - 1) / B;
+  c->chunk_end[3] = c->chunk_end[2] + (inj + B - 1) / B;
+  c->K = (live + inj < S->tail_threshold) ? S->K_tail : S->K_bulk;
+  c->cnt[pn ^ 1][0] = c->cnt[pn ^ 1][1] = c->cnt[pn ^ 1][2] = 0;
+  c->claim = 0;
+  c->blocks_done = 0;
+  if (live + inj > c->live_peak) c->live_peak = live + inj;
+  if (live + inj > 0) c->gen += 1;
+  if (c->gen > S->max_gen && c->status == 0) c->status = GV_ERR_TIMEOUT;
+  c->done = (c->status != 0) || (live == 0 && inj == 0 && c->prim_next == S->n_prim);
+  if (c->done) c->chunk_end[0] = c->chunk_end[1] = c->chunk_end[2] = c->chunk_end[3] = 0;
+  c->counters[GV_C_GENERATIONS] = c->gen;
+}
+
+template <typename R> __global__ void init_kernel(const DevState<R> *S) {
+  Ctl *c = S->ctl;
+  for (int i = 0; i < 2; ++i)
+    for (int q = 0; q < 3; ++q) c->cnt[i][q] = 0;
+  c->prim_next = 0;
+  c->status = 0;
+  c->done = 0;
+  c->gen = 0;
+  c->live_peak = 0;
+  for (int i = 0; i < 16; ++i) c->counters[i] = 0;
+  plan_next(S, 0);
+}
+
+// ------------------------------------------------------------------ the kernel
+template <typename R> __global__ void __launch_bounds__(512) step_kernel(const DevState<R> *__restrict__ S, int parity) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ View<R> sV;
+  __shared__ BlockCnt bc;
+  __shared__ unsigned s_chunk, s_end[4], s_pb;
+  __shared__ int s_K, s_last;
+  Ctl *ctl = S->ctl;
+  const int tid = threadIdx.x;
+  if (ctl->done) return;  // uniform: nothing planned for this generation
+  // stage the cross-section tables and the geometry into shared memory
+  {
+    const uint4 *src = reinterpret_cast<const uint4 *>(S->view.xs);
+    uint4 *dst = reinterpret_cast<uint4 *>(smem);
+    for (unsigned i = tid; i < S->xs_bytes / 16; i += blockDim.x) dst[i] = src[i];
+    const double *zsrc = S->view.zb;
+    double *zdst = reinterpret_cast<double *>(smem + S->xs_bytes);
+    const int nz = S->view.geo.nsub + 1;
+    for (int i = tid; i < nz; i += blockDim.x) zdst[i] = zsrc[i];
+    unsigned char *mdst = smem + S->xs_bytes + S->zb_bytes;
+    for (int i = tid; i < S->view.geo.nsub; i += blockDim.x) mdst[i] = S->view.smat[i];
+    if (tid == 0) {
+      sV = S->view;
+      sV.xs = reinterpret_cast<const V4<R> *>(smem);
+      sV.zb = zdst;
+      sV.smat = mdst;
+      for (int i = 0; i < 4; ++i) s_end[i] = ctl->chunk_end[i];
+      s_pb = ctl->prim_begin;
+      s_K = ctl->K;
+    }
+    if (tid < 16) bc.c[tid] = 0;
+  }
+  __syncthreads();
+  const View<R> &V = sV;
+  const int in = parity, out = parity ^ 1;
+  const unsigned cap = static_cast<unsigned>(S->capacity);
+  const unsigned n_in[3] = {min(ctl->cnt[in][0], cap), min(ctl->cnt[in][1], cap), min(ctl->cnt[in][2], cap)};
+  const unsigned n_prim_gen = ctl->prim_count;
+  for (;;) {
+    if (tid == 0) s_chunk = atomicAdd(&ctl->claim, 1u);
+    __syncthreads();
+    const unsigned chunk = s_chunk;
+    __syncthreads();
+    if (chunk >= s_end[3]) break;
+    int qsel = 0;
+    while (chunk >= s_end[qsel]) ++qsel;
+    const unsigned first = (chunk - (qsel ? s_end[qsel - 1] : 0u)) * blockDim.x;
+    const unsigned idx = first + tid;
+    Trk<R> t;
+    bool alive = false;
+    if (qsel < 3) {
+      if (idx < n_in[qsel]) {
+        const Queue<R> &q = S->q[in][qsel];
+        t.x = q.x[idx]; t.y = q.y[idx]; t.z = q.z[idx];
+        t.u = q.u[idx]; t.v = q.v[idx]; t.w = q.w[idx];
+        t.E = q.E[idx]; t.nlam = q.nlam[idx];
+        t.id = q.id[idx]; t.ev = q.ev[idx]; t.step = q.step[idx];
+        const int sf = q.sf[idx];
+        t.sub = sf & 0xffff;
+        t.flags = sf >> 16;
+        t.type = qsel;
+        alive = true;
+      }
+    } else if (idx < n_prim_gen) {
+      const unsigned i = s_pb + idx;
+      const unsigned pi = S->order ? S->order[i] : i;
+      gv_primary p = S->prim[pi];
+      if (p.type < 0 || p.type > 2 || p.event >= S->n_events) {  // caller's device array: check here
+        set_status(ctl, GV_ERR_BAD_ARG);
+        p.type = 0;
+        p.event = 0;
+        p.z = -1.0;
+        p.E_MeV = 0.0;
+      }
+      t.type = p.type;
+      t.E = static_cast<R>(p.E_MeV);
+      t.x = p.x; t.y = p.y; t.z = p.z;
+      t.u = static_cast<R>(p.u); t.v = static_cast<R>(p.v); t.w = static_cast<R>(p.w);
+      t.nlam = R(-1);
+      t.id = pi;
+      t.ev = p.event;
+      t.step = 0;
+      t.flags = kFlagPrimary;
+      t.sub = locate(V.zb, V.geo.nsub, p.z, p.w);
+      count(S, &bc, t.ev, GV_C_TRK_G + t.type);
+      if (t.sub < 0) {
+        atomicAdd(&S->escape[t.ev], p.E_MeV);
+        if (t.type == 2) count(S, &bc, t.ev, GV_C_EP_ESC);
+      } else {
+        alive = true;
+      }
+    }
+    const int K = s_K;
+    for (int kk = 0; kk < K; ++kk) {
+      if (!__any_sync(0xffffffffu, alive)) break;
+      Kids<R> kids;
+      kids.n = 0;
+      uint32_t kstep = 0;
+      if (alive) {
+        alive = step_track(V, S, t, kids, kstep, &bc) != 0;
+        if (!(t.E == t.E) || !(t.z == t.z)) {
+          set_status(ctl, GV_ERR_NUMERIC);
+          alive = false;
+        }
+      }
+      push_kids(S, out, t, kids, kstep, &bc);
+    }
+    push_survivor(S, out, t, alive);
+  }
+  // flush block counters; the last block plans the next generation
+  __syncthreads();
+  if (tid < 16 && bc.c[tid]) atomicAdd(&ctl->counters[tid], bc.c[tid]);
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(&ctl->blocks_done, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last && tid == 0) {
+    __threadfence();
+    plan_next(S, out);
+  }
+}
+
+}  // namespace gv
+
+// ====================================================================== host
+using namespace gv;
+
+namespace {
+
+struct Ctx {
+  int device = 0, sm_count = 0;
+  gv_config cfg;
+  std::vector<gv_material> mats;
+  gv_layers geo;
+  gv_cuts cuts;
+  int nsub = 0;
+  std::vector<double> zb;
+  std::vector<unsigned char> smat;
+  bool tables = false;
+  HostTables ht;
+  // device allocations
+  void *d_xs = nullptr, *d_bins = nullptr;
+  double *d_zb = nullptr;
+  unsigned char *d_smat = nullptr;
+  void *d_queues = nullptr;
+  Ctl *d_ctl = nullptr;
+  void *d_state = nullptr;
+  double *d_edep = nullptr, *d_cell = nullptr, *d_escape = nullptr;
+  unsigned long long *d_evcnt = nullptr;
+  size_t ev_cap = 0;
+  gv_primary *d_prim = nullptr;
+  unsigned *d_order = nullptr;
+  size_t prim_cap = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  Ctl *h_ctl = nullptr;  // pinned
+  long long launches = 0;
+  int last_status = 0;
+  ModelMeta meta[kNModel];
+  size_t xs_bytes = 0, zb_bytes = 0, smem_bytes = 0;
+  int grid = 0;
+};
+
+#define CK(x)                                  \
+  do {                                         \
+    cudaError_t e_ = (x);                      \
+    if (e_ != cudaSuccess) return GV_ERR_CUDA; \
+  } while (0)
+
+int validate(const gv_material *mats, int n_mats, const gv_layers *geo, const gv_cuts *cuts) {
+  if (!mats || !geo || !cuts || n_mats < 1 || n_mats > GV_MAX_MAT) return GV_ERR_BAD_ARG;
+  for (int m = 0; m < n_mats; ++m) {
+    const gv_material &x = mats[m];
+    if (x.n_elem < 1 || x.n_elem > GV_MAX_ELEM || !(x.rho > 0) || !(x.I_eV > 0)) return GV_ERR_BAD_ARG;
+    for (int e = 0; e < x.n_elem; ++e)
+      if (!(x.Z[e] >= 1) || !(x.A[e] > 0) || !(x.w[e] > 0)) return GV_ERR_BAD_ARG;
+  }
+  if (geo->n_layers < 1 || geo->n_sub < 1 || geo->n_sub > GV_MAX_SUB ||
+      static_cast<long long>(geo->n_layers) * geo->n_sub > GV_MAX_SUBTOTAL)
+    return GV_ERR_BAD_ARG;
+  for (int j = 0; j < geo->n_sub; ++j)
+    if (!(geo->sub_thick_cm[j] > 0) || geo->sub_mat[j] < 0 || geo->sub_mat[j] >= n_mats) return GV_ERR_BAD_ARG;
+  if (geo->nx_cells < 0 || geo->ny_cells < 0) return GV_ERR_BAD_ARG;
+  if ((geo->nx_cells > 0 || geo->ny_cells > 0) &&
+      !(geo->nx_cells > 0 && geo->ny_cells > 0 && geo->half_x_cm > 0 && geo->half_y_cm > 0))
+    return GV_ERR_BAD_ARG;
+  if (!(cuts->track_cut_MeV >= kGridEmin) || !(cuts->gamma_cut_MeV >= cuts->track_cut_MeV) ||
+      !(cuts->e_cut_MeV >= cuts->track_cut_MeV))
+    return GV_ERR_BAD_ARG;
+  return GV_OK;
+}
+
+int validate_cfg(const gv_config &c) {
+  if (c.precision != GV_MIXED && c.precision != GV_FP64) return GV_ERR_BAD_ARG;
+  if (c.mode != GV_BATCHED && c.mode != GV_ONE_EVENT_PER_LAUNCH) return GV_ERR_BAD_ARG;
+  if (c.block_size < 64 || c.block_size > 512 || c.block_size % 32) return GV_ERR_BAD_ARG;
+  if (c.blocks_per_sm < 1 || c.blocks_per_sm > 32) return GV_ERR_BAD_ARG;
+  if (c.steps_per_claim < 1 || c.tail_steps_per_claim < 1 || c.steps_per_claim > 4096 ||
+      c.tail_steps_per_claim > 4096)
+    return GV_ERR_BAD_ARG;
+  if (c.stack_capacity < 1024 || c.stack_capacity > (1ll << 31)) return GV_ERR_BAD_ARG;
+  if (c.refill_batch < 1 || c.refill_low_water < 0) return GV_ERR_BAD_ARG;
+  if (c.generations_per_graph < 2 || c.generations_per_graph % 2 || c.generations_per_graph > 1024)
+    return GV_ERR_BAD_ARG;
+  if (c.max_generations < 1) return GV_ERR_BAD_ARG;
+  return GV_OK;
+}
+
+template <typename R> size_t queue_bytes(long long cap) { return static_cast<size_t>(cap) * track_bytes<R>(); }
+
+template <typename R> Queue<R> carve(unsigned char *&p, long long cap) {
+  Queue<R> q;
+  auto take = [&](size_t n) {
+    unsigned char *r = p;
+    p += (n + 255) / 256 * 256;
+    return r;
+  };
+  q.x = reinterpret_cast<double *>(take(cap * sizeof(double)));
+  q.y = reinterpret_cast<double *>(take(cap * sizeof(double)));
+  q.z = reinterpret_cast<double *>(take(cap * sizeof(double)));
+  q.u = reinterpret_cast<R *>(take(cap * sizeof(R)));
+  q.v = reinterpret_cast<R *>(take(cap * sizeof(R)));
+  q.w = reinterpret_cast<R *>(take(cap * sizeof(R)));
+  q.E = reinterpret_cast<R *>(take(cap * sizeof(R)));
+  q.nlam = reinterpret_cast<R *>(take(cap * sizeof(R)));
+  q.id = reinterpret_cast<unsigned long long *>(take(cap * sizeof(unsigned long long)));
+  q.ev = reinterpret_cast<unsigned *>(take(cap * sizeof(unsigned)));
+  q.step = reinterpret_cast<unsigned *>(take(cap * sizeof(unsigned)));
+  q.sf = reinterpret_cast<int *>(take(cap * sizeof(int)));
+  return q;
+}
+
+template <typename R> size_t carve_bytes(long long cap) {
+  size_t s = 0;
+  const size_t sizes[12] = {8, 8, 8, sizeof(R), sizeof(R), sizeof(R), sizeof(R), sizeof(R), 8, 4, 4, 4};
+  for (size_t z : sizes) s += (cap * z + 255) / 256 * 256;
+  return s;
+}
+
+template <typename R> int upload_tables(Ctx *c) {
+  const HostTables &h = c->ht;
+  // cross sections as V4<R>
+  const size_t nv = static_cast<size_t>(h.n_mat) * 3 * kGridN;
+  std::vector<V4<R>> xs(nv);
+  for (size_t i = 0; i < nv; ++i) {
+    xs[i].x = static_cast<R>(h.xs[4 * i + 0]);
+    xs[i].y = static_cast<R>(h.xs[4 * i + 1]);
+    xs[i].z = static_cast<R>(h.xs[4 * i + 2]);
+    xs[i].w = static_cast<R>(h.xs[4 * i + 3]);
+  }
+  c->xs_bytes = nv * sizeof(V4<R>);
+  CK(cudaMalloc(&c->d_xs, c->xs_bytes));
+  CK(cudaMemcpy(c->d_xs, xs.data(), c->xs_bytes, cudaMemcpyHostToDevice));
+  // alias bins
+  std::vector<AliasBin<R>> bins;
+  for (int m = 0; m < kNModel; ++m) {
+    c->meta[m].ln_Elo = std::log(h.a_Elo[m]);
+    c->meta[m].inv_dl = kAliasPerDecade / std::log(10.0);
+    c->meta[m].cut = h.a_cut[m];
+    c->meta[m].nE = h.a_nE[m];
+    c->meta[m].off = static_cast<int>(bins.size());
+    for (int ie = 0; ie < h.a_nE[m]; ++ie)
+      for (int j = 0; j < kNB; ++j) {
+        AliasBin<R> b;
+        b.q = h.a_q[m][static_cast<size_t>(ie) * kNB + j];
+        b.a = h.a_alias[m][static_cast<size_t>(ie) * kNB + j];
+        b.p0 = static_cast<R>(h.a_pdf[m][static_cast<size_t>(ie) * (kNB + 1) + j]);
+        b.p1 = static_cast<R>(h.a_pdf[m][static_cast<size_t>(ie) * (kNB + 1) + j + 1]);
+        bins.push_back(b);
+      }
+  }
+  CK(cudaMalloc(&c->d_bins, bins.size() * sizeof(AliasBin<R>)));
+  CK(cudaMemcpy(c->d_bins, bins.data(), bins.size() * sizeof(AliasBin<R>), cudaMemcpyHostToDevice));
+  return GV_OK;
+}
+
+template <typename R> View<R> make_view(const Ctx *c) {
+  View<R> v;
+  v.xs = reinterpret_cast<const V4<R> *>(c->d_xs);
+  v.zb = c->d_zb;
+  v.smat = c->d_smat;
+  v.bins = reinterpret_cast<const AliasBin<R> *>(c->d_bins);
+  for (int m = 0; m < kNModel; ++m) v.meta[m] = c->meta[m];
+  v.geo.nsub = c->nsub;
+  v.geo.nsub_layer = c->geo.n_sub;
+  v.geo.n_layers = c->geo.n_layers;
+  v.geo.nx = c->geo.nx_cells;
+  v.geo.ny = c->geo.ny_cells;
+  v.geo.hx = c->geo.half_x_cm;
+  v.geo.hy = c->geo.half_y_cm;
+  v.geo.pitch_x = c->geo.nx_cells > 0 ? 2.0 * c->geo.half_x_cm / c->geo.nx_cells : 1.0;
+  v.geo.pitch_y = c->geo.ny_cells > 0 ? 2.0 * c->geo.half_y_cm / c->geo.ny_cells : 1.0;
+  v.cut.gcut = c->cuts.gamma_cut_MeV;
+  v.cut.ecut = c->cuts.e_cut_MeV;
+  v.cut.tcut = c->cuts.track_cut_MeV;
+  v.cut.mask = c->cuts.process_mask;
+  return v;
+}
+
+template <typename R> int prepare_device(Ctx *c) {
+  CK(cudaSetDevice(c->device));
+  int rc = upload_tables<R>(c);
+  if (rc) return rc;
+  const long long cap = c->cfg.stack_capacity;
+  const size_t per = carve_bytes<R>(cap);
+  if (cudaMalloc(&c->d_queues, per * 6) != cudaSuccess) return GV_ERR_OOM;
+  CK(cudaMalloc(&c->d_ctl, sizeof(Ctl)));
+  CK(cudaMemset(c->d_ctl, 0, sizeof(Ctl)));
+  CK(cudaMalloc(&c->d_state, sizeof(DevState<R>)));
+  CK(cudaMallocHost(&c->h_ctl, sizeof(Ctl)));
+  c->zb_bytes = ((c->nsub + 1) * sizeof(double) + 15) / 16 * 16;
+  c->smem_bytes = c->xs_bytes + c->zb_bytes + (c->nsub + 15) / 16 * 16;
+  CK(cudaFuncSetAttribute(step_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          static_cast<int>(c->smem_bytes)));
+  int occ = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_kernel<R>, c->cfg.block_size, c->smem_bytes));
+  if (occ < 1) return GV_ERR_BAD_ARG;
+  c->grid = c->sm_count * std::min(occ, c->cfg.blocks_per_sm);
+  return GV_OK;
+}
+
+template <typename R> DevState<R> make_state(Ctx *c) {
+  DevState<R> s;
+  std::memset(&s, 0, sizeof(s));
+  s.view = make_view<R>(c);
+  unsigned char *p = static_cast<unsigned char *>(c->d_queues);
+  for (int par = 0; par < 2; ++par)
+    for (int q = 0; q < 3; ++q) s.q[par][q] = carve<R>(p, c->cfg.stack_capacity);
+  s.capacity = static_cast<unsigned long long>(c->cfg.stack_capacity);
+  s.ctl = c->d_ctl;
+  s.block_size = c->cfg.block_size;
+  s.mode = c->cfg.mode;
+  s.K_bulk = c->cfg.steps_per_claim;
+  s.K_tail = c->cfg.tail_steps_per_claim;
+  s.tail_threshold = static_cast<unsigned long long>(c->cfg.tail_threshold);
+  s.low_water = static_cast<unsigned long long>(c->cfg.mode == GV_ONE_EVENT_PER_LAUNCH ? 1 : c->cfg.refill_low_water);
+  s.batch = static_cast<unsigned long long>(c->cfg.refill_batch);
+  s.max_gen = static_cast<unsigned long long>(c->cfg.max_generations);
+  s.n_mat = static_cast<int>(c->mats.size());
+  s.xs_bytes = static_cast<unsigned>(c->xs_bytes);
+  s.zb_bytes = static_cast<unsigned>(c->zb_bytes);
+  return s;
+}
+
+template <typename R> int capture_graph(Ctx *c) {
+  if (c->graph) return GV_OK;
+  cudaGraph_t g;
+  CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  const DevState<R> *S = reinterpret_cast<const DevState<R> *>(c->d_state);
+  for (int i = 0; i < c->cfg.generations_per_graph; ++i)
+    step_kernel<R><<<c->grid, c->cfg.block_size, c->smem_bytes, c->stream>>>(S, i & 1);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (e != cudaSuccess) return GV_ERR_CUDA;
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  return e == cudaSuccess ? GV_OK : GV_ERR_CUDA;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename R>
+int run_transport(Ctx *c, const gv_primary *p, long long n, long long n_events, unsigned long long seed,
+                  cudaStream_t user, gv_result *res) {
+  CK(cudaSetDevice(c->device));
+  const int nsub = c->nsub;
+  const size_t ncell = static_cast<size_t>(c->geo.n_layers) * c->geo.nx_cells * c->geo.ny_cells;
+  if (static_cast<size_t>(n_events) > c->ev_cap) {
+    cudaFree(c->d_edep);
+    cudaFree(c->d_escape);
+    cudaFree(c->d_evcnt);
+    c->d_edep = nullptr;
+    c->d_escape = nullptr;
+    c->d_evcnt = nullptr;
+    c->ev_cap = 0;
+    if (cudaMalloc(&c->d_edep, sizeof(double) * n_events * nsub) != cudaSuccess ||
+        cudaMalloc(&c->d_escape, sizeof(double) * n_events) != cudaSuccess ||
+        cudaMalloc(&c->d_evcnt, sizeof(unsigned long long) * n_events * GV_NCOUNT) != cudaSuccess)
+      return GV_ERR_OOM;
+    c->ev_cap = n_events;
+  }
+  if (ncell && !c->d_cell) {
+    if (cudaMalloc(&c->d_cell, sizeof(double) * ncell) != cudaSuccess) return GV_ERR_OOM;
+  }
+  const bool dev_prim = is_device_ptr(p);
+  std::vector<unsigned> order;
+  if (c->cfg.mode == GV_ONE_EVENT_PER_LAUNCH || !dev_prim) {
+    if (static_cast<size_t>(n) > c->prim_cap) {
+      cudaFree(c->d_prim);
+      cudaFree(c->d_order);
+      c->d_prim = nullptr;
+      c->d_order = nullptr;
+      if (cudaMalloc(&c->d_prim, sizeof(gv_primary) * n) != cudaSuccess ||
+          cudaMalloc(&c->d_order, sizeof(unsigned) * n) != cudaSuccess)
+        return GV_ERR_OOM;
+      c->prim_cap = n;
+    }
+  }
+  // the work stream waits for whatever the caller queued before
+  CK(cudaEventRecord(c->ev_in, user));
+  CK(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+  const gv_primary *dp = p;
+  std::vector<gv_primary> hp;
+  if (!dev_prim) {
+    CK(cudaMemcpyAsync(c->d_prim, p, sizeof(gv_primary) * n, cudaMemcpyHostToDevice, c->stream));
+    dp = c->d_prim;
+  }
+  if (c->cfg.mode == GV_ONE_EVENT_PER_LAUNCH) {
+    if (dev_prim) {
+      hp.resize(n);
+      CK(cudaMemcpyAsync(hp.data(), p, sizeof(gv_primary) * n, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+    }
+    const gv_primary *src = dev_prim ? hp.data() : p;
+    order.resize(n);
+    for (long long i = 0; i < n; ++i) order[i] = static_cast<unsigned>(i);
+    std::stable_sort(order.begin(), order.end(), [src](unsigned a, unsigned b) { return src[a].event < src[b].event; });
+    CK(cudaMemcpyAsync(c->d_order, order.data(), sizeof(unsigned) * n, cudaMemcpyHostToDevice, c->stream));
+  }
+  CK(cudaMemsetAsync(c->d_edep, 0, sizeof(double) * n_events * nsub, c->stream));
+  CK(cudaMemsetAsync(c->d_escape, 0, sizeof(double) * n_events, c->stream));
+  if (ncell) CK(cudaMemsetAsync(c->d_cell, 0, sizeof(double) * ncell, c->stream));
+  const bool evc = c->cfg.per_event_counts != 0 && res && res->event_counts;
+  if (evc) CK(cudaMemsetAsync(c->d_evcnt, 0, sizeof(unsigned long long) * n_events * GV_NCOUNT, c->stream));
+  DevState<R> s = make_state<R>(c);
+  s.prim = dp;
+  s.order = c->cfg.mode == GV_ONE_EVENT_PER_LAUNCH ? c->d_order : nullptr;
+  s.n_prim = static_cast<unsigned>(n);
+  s.n_events = static_cast<unsigned>(n_events);
+  s.edep = c->d_edep;
+  s.cell = (ncell && res && res->cell_edep) ? c->d_cell : nullptr;
+  s.escape = c->d_escape;
+  s.evcnt = evc ? c->d_evcnt : nullptr;
+  s.seed_lo = static_cast<unsigned>(seed);
+  s.seed_hi = static_cast<unsigned>(seed >> 32);
+  static thread_local DevState<R> staged;  // pinned copy not needed: synchronous below
+  staged = s;
+  CK(cudaMemcpyAsync(c->d_state, &staged, sizeof(s), cudaMemcpyHostToDevice, c->stream));
+  const DevState<R> *S = reinterpret_cast<const DevState<R> *>(c->d_state);
+  init_kernel<R><<<1, 1, 0, c->stream>>>(S);
+  CK(cudaGetLastError());
+  int rc = capture_graph<R>(c);
+  if (rc) return rc;
+  long long launches = 1;
+  int between = 1;
+  double kernel_ms = 0.0;
+  for (;;) {
+    CK(cudaEventRecord(c->t0, c->stream));
+    for (int i = 0; i < between; ++i) CK(cudaGraphLaunch(c->graph, c->stream));
+    CK(cudaEventRecord(c->t1, c->stream));
+    launches += static_cast<long long>(between) * c->cfg.generations_per_graph;
+    CK(cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->t0, c->t1));
+    kernel_ms += ms;
+    if (c->h_ctl->done) break;
+    between = std::min(between * 2, 64);
+  }
+  c->launches = launches;
+  const Ctl &h = *c->h_ctl;
+  int status = h.status;
+  if (res) {
+    for (int i = 0; i < 16; ++i) res->counters[i] = h.counters[i];
+    res->counters[GV_C_GENERATIONS] = h.gen;
+    res->counters[15] = h.live_peak;
+    if (res->edep)
+      CK(cudaMemcpyAsync(res->edep, c->d_edep, sizeof(double) * n_events * nsub, cudaMemcpyDefault, c->stream));
+    if (res->escape_E)
+      CK(cudaMemcpyAsync(res->escape_E, c->d_escape, sizeof(double) * n_events, cudaMemcpyDefault, c->stream));
+    if (res->cell_edep && ncell)
+      CK(cudaMemcpyAsync(res->cell_edep, c->d_cell, sizeof(double) * ncell, cudaMemcpyDefault, c->stream));
+    if (evc)
+      CK(cudaMemcpyAsync(res->event_counts, c->d_evcnt, sizeof(long long) * n_events * GV_NCOUNT, cudaMemcpyDefault,
+                         c->stream));
+    res->status = status;
+    res->kernel_ms = kernel_ms;
+  }
+  CK(cudaEventRecord(c->ev_out, c->stream));
+  CK(cudaStreamWaitEvent(user, c->ev_out, 0));
+  CK(cudaStreamSynchronize(c->stream));
+  c->last_status = status;
+  return status;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+int gv_default_config(gv_config *cfg) {
+  if (!cfg) return GV_ERR_BAD_ARG;
+  cfg->precision = GV_MIXED;
+  cfg->mode = GV_BATCHED;
+  cfg->block_size = 256;
+  cfg->blocks_per_sm = 4;
+  cfg->steps_per_claim = 4;
+  cfg->tail_steps_per_claim = 64;
+  cfg->tail_threshold = 100000;
+  cfg->stack_capacity = 1ll << 23;
+  cfg->refill_low_water = 1ll << 21;
+  cfg->refill_batch = 1ll << 14;
+  cfg->generations_per_graph = 16;
+  cfg->max_generations = 1ll << 20;
+  cfg->per_event_counts = 0;
+  cfg->process_sort = 0;
+  return GV_OK;
+}
+
+int gv_setup(void **ctx_out, const gv_material *mats, int n_mats, const gv_layers *geo, const gv_cuts *cuts,
+             const gv_config *cfg) {
+  if (!ctx_out) return GV_ERR_BAD_ARG;
+  *ctx_out = nullptr;
+  int rc = validate(mats, n_mats, geo, cuts);
+  if (rc) return rc;
+  gv_config c;
+  gv_default_config(&c);
+  if (cfg) c = *cfg;
+  rc = validate_cfg(c);
+  if (rc) return rc;
+  Ctx *x = new Ctx();
+  x->cfg = c;
+  x->mats.assign(mats, mats + n_mats);
+  x->geo = *geo;
+  x->cuts = *cuts;
+  x->nsub = geo->n_layers * geo->n_sub;
+  x->zb.resize(x->nsub + 1);
+  x->smat.resize(x->nsub);
+  double z = 0.0;
+  x->zb[0] = 0.0;
+  for (int l = 0; l < geo->n_layers; ++l)
+    for (int j = 0; j < geo->n_sub; ++j) {
+      const int k = l * geo->n_sub + j;
+      z += geo->sub_thick_cm[j];
+      x->zb[k + 1] = z;
+      x->smat[k] = static_cast<unsigned char>(geo->sub_mat[j]);
+    }
+  if (cudaGetDevice(&x->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&x->sm_count, cudaDevAttrMultiProcessorCount, x->device) != cudaSuccess) {
+    delete x;
+    return GV_ERR_CUDA;
+  }
+  if (cudaMalloc(&x->d_zb, sizeof(double) * (x->nsub + 1)) != cudaSuccess ||
+      cudaMalloc(&x->d_smat, x->nsub) != cudaSuccess ||
+      cudaMemcpy(x->d_zb, x->zb.data(), sizeof(double) * (x->nsub + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(x->d_smat, x->smat.data(), x->nsub, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&x->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&x->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&x->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&x->t0) != cudaSuccess || cudaEventCreate(&x->t1) != cudaSuccess) {
+    gv_destroy(x);
+    return GV_ERR_CUDA;
+  }
+  *ctx_out = x;
+  return GV_OK;
+}
+
+int gv_build_tables(void *ctx) {
+  Ctx *c = static_cast<Ctx *>(ctx);
+  if (!c) return GV_ERR_BAD_ARG;
+  if (c->tables) return GV_OK;
+  std::string err;
+  int rc = build_host_tables(c->mats.data(), static_cast<int>(c->mats.size()), c->cuts, &c->ht, &err);
+  if (rc) return rc;
+  rc = c->cfg.precision == GV_FP64 ? prepare_device<double>(c) : prepare_device<float>(c);
+  if (rc) return rc;
+  c->tables = true;
+  return GV_OK;
+}
+
+int gv_transport(void *ctx, const gv_primary *p, long long n, long long n_events, unsigned long long seed,
+                 void *stream, gv_result *res) {
+  Ctx *c = static_cast<Ctx *>(ctx);
+  if (!c || (!p && n > 0) || n < 0 || n_events < 1 || n > 0xffffffffll || n_events > 0xffffffffll)
+    return GV_ERR_BAD_ARG;
+  if (!c->tables) return GV_ERR_NO_TABLES;
+  if (!res || !res->edep) return GV_ERR_BAD_ARG;
+  if (res->event_counts && !c->cfg.per_event_counts) return GV_ERR_BAD_ARG;
+  if (!is_device_ptr(p)) {
+    for (long long i = 0; i < n; ++i)
+      if (p[i].type < 0 || p[i].type > 2 || p[i].event >= static_cast<unsigned long long>(n_events) ||
+          !(p[i].E_MeV >= 0))
+        return GV_ERR_BAD_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return c->cfg.precision == GV_FP64 ? run_transport<double>(c, p, n, n_events, seed, s, res)
+                                     : run_transport<float>(c, p, n, n_events, seed, s, res);
+}
+
+int gv_sync(void *ctx, void *stream) {
+  Ctx *c = static_cast<Ctx *>(ctx);
+  if (!c) return GV_ERR_BAD_ARG;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return GV_ERR_CUDA;
+  return c->last_status;
+}
+
+long long gv_last_launches(void *ctx) {
+  Ctx *c = static_cast<Ctx *>(ctx);
+  return c ? c->launches : -1;
+}
+
+void gv_destroy(void *ctx) {
+  Ctx *c = static_cast<Ctx *>(ctx);
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  cudaFree(c->d_xs);
+  cudaFree(c->d_bins);
+  cudaFree(c->d_zb);
+  cudaFree(c->d_smat);
+  cudaFree(c->d_queues);
+  cudaFree(c->d_ctl);
+  cudaFree(c->d_state);
+  cudaFree(c->d_edep);
+  cudaFree(c->d_cell);
+  cudaFree(c->d_escape);
+  cudaFree(c->d_evcnt);
+  cudaFree(c->d_prim);
+  cudaFree(c->d_order);
+  if (c->h_ctl) cudaFreeHost(c->h_ctl);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->t0) cudaEventDestroy(c->t0);
+  if (c->t1) cudaEventDestroy(c->t1);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char *gv_strerror(int code) {
+  switch (code) {
+    case GV_OK: return "ok";
+    case GV_ERR_BAD_ARG: return "bad argument";
+    case GV_ERR_NO_TABLES: return "tables not built";
+    case GV_ERR_OOM: return "device allocation failed";
+    case GV_ERR_STACK_FULL: return "track queue overflow";
+    case GV_ERR_TIMEOUT: return "generation budget exhausted";
+    case GV_ERR_NUMERIC: return "non-finite track state";
+    case GV_ERR_CUDA: return "CUDA runtime error";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"
+
+// exported for the element-wise entry points (gv_unit.cu)
+namespace gv {
+int ctx_views(void *ctx, int *precision, View<float> *vf, View<double> *vd) {
+  Ctx *c = static_cast<Ctx *>(ctx);
+  if (!c) return GV_ERR_BAD_ARG;
+  if (!c->tables) return GV_ERR_NO_TABLES;
+  *precision = c->cfg.precision;
+  if (c->cfg.precision == GV_FP64) *vd = make_view<double>(c);
+  else *vf = make_view<float>(c);
+  return GV_OK;
+}
+int ctx_nmat(void *ctx) { return static_cast<int>(static_cast<Ctx *>(ctx)->mats.size()); }
+}  // namespace gv

@@ -1,0 +1,179 @@
+// gv_unit.cu -- element-wise entry points over the device functions of one
+// transport step: Philox, table lookup, continuous loss, alias sampling,
+// final states and the slab navigator.  Each runs one element per thread in
+// the context's precision, reading the tables from global memory.
+#include <cuda_runtime.h>
+
+#include "gv_device.cuh"
+
+namespace gv {
+int ctx_views(void *ctx, int *precision, View<float> *vf, View<double> *vd);
+int ctx_nmat(void *ctx);
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int blocks_for(long long n) { return static_cast<int>((n + kThreads - 1) / kThreads); }
+
+__global__ void k_philox(const unsigned *ctr, const unsigned *key, unsigned *out, long long n) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+  const uint4 r = philox4x32_10(c, key[2 * i], key[2 * i + 1]);
+  out[4 * i] = r.x;
+  out[4 * i + 1] = r.y;
+  out[4 * i + 2] = r.z;
+  out[4 * i + 3] = r.w;
+}
+
+template <typename R>
+__global__ void k_lookup(View<R> V, int type, int mat, const double *E, long long n, double *out) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const V4<R> v = lookup(V, mat, type, static_cast<R>(E[i]));
+  out[4 * i] = v.x;
+  out[4 * i + 1] = v.y;
+  out[4 * i + 2] = v.z;
+  out[4 * i + 3] = v.w;
+}
+
+template <typename R>
+__global__ void k_eloss(View<R> V, int type, int mat, const double *E, const double *s, long long n, double *out) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  out[i] = eloss(V, mat, type, static_cast<R>(E[i]), static_cast<R>(s[i]));
+}
+
+template <typename R>
+__global__ void k_alias(View<R> V, int model, const double *E, const double *u, long long n, double *out) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  R xi;
+  const R v = alias_sample<R>(V, model, static_cast<R>(E[i]), static_cast<R>(u[3 * i]), static_cast<R>(u[3 * i + 1]),
+                              static_cast<R>(u[3 * i + 2]), &xi);
+  out[2 * i] = v;
+  out[2 * i + 1] = xi;
+}
+
+template <typename R>
+__global__ void k_interact(View<R> V, int type, int proc, const double *E, const double *dir, const double *u,
+                           long long n, double *out, int *ret) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  R e = static_cast<R>(E[i]);
+  R d[3] = {static_cast<R>(dir[3 * i]), static_cast<R>(dir[3 * i + 1]), static_cast<R>(dir[3 * i + 2])};
+  R uu[8];
+  for (int j = 0; j < 8; ++j) uu[j] = static_cast<R>(u[8 * i + j]);
+  Kids<R> kids;
+  kids.n = 0;
+  R local = R(0);
+  int np = 0, na = 0;
+  const int r = interact(V, type, proc, e, d, uu, kids, local, np, na);
+  double *o = out + 24 * i;
+  for (int j = 0; j < 24; ++j) o[j] = 0.0;
+  o[0] = r == 1 ? static_cast<double>(e) : (r == 0 ? -1.0 : E[i]);
+  o[1] = d[0];
+  o[2] = d[1];
+  o[3] = d[2];
+  o[4] = local;
+  o[5] = kids.n;
+  for (int j = 0; j < kids.n; ++j) {
+    o[6 + 5 * j] = kids.type[j];
+    o[7 + 5 * j] = kids.E[j];
+    o[8 + 5 * j] = kids.d[j][0];
+    o[9 + 5 * j] = kids.d[j][1];
+    o[10 + 5 * j] = kids.d[j][2];
+  }
+  ret[i] = r;
+}
+
+template <typename R>
+__global__ void k_distance(View<R> V, const double *pos, const double *dir, const int *sub, long long n, double *dist,
+                           int *next, int *plane) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  int nx, pl;
+  if (sub[i] < 0 || sub[i] >= V.geo.nsub) {  // not a sub-slab: report, touch no table
+    dist[i] = -1.0;
+    next[i] = -1;
+    plane[i] = -1;
+    return;
+  }
+  const R d = distance(V, pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], static_cast<R>(dir[3 * i]),
+                       static_cast<R>(dir[3 * i + 1]), static_cast<R>(dir[3 * i + 2]), sub[i], nx, pl);
+  dist[i] = d;
+  next[i] = nx;
+  plane[i] = pl;
+}
+
+int launch_status() { return cudaGetLastError() == cudaSuccess ? GV_OK : GV_ERR_CUDA; }
+
+}  // namespace
+}  // namespace gv
+
+using namespace gv;
+
+extern "C" {
+
+int gv_unit_philox(const unsigned *ctr, const unsigned *key, unsigned *out, long long n, void *stream) {
+  if (n < 0 || (n > 0 && (!ctr || !key || !out))) return GV_ERR_BAD_ARG;
+  if (n == 0) return GV_OK;
+  k_philox<<<blocks_for(n), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(ctr, key, out, n);
+  return launch_status();
+}
+
+#define GV_UNIT_DISPATCH(launch_f, launch_d)        \
+  int prec;                                         \
+  View<float> vf;                                   \
+  View<double> vd;                                  \
+  int rc = ctx_views(ctx, &prec, &vf, &vd);         \
+  if (rc) return rc;                                \
+  cudaStream_t s = static_cast<cudaStream_t>(stream); \
+  if (prec == GV_FP64) { launch_d; } else { launch_f; } \
+  return launch_status();
+
+int gv_unit_xs_lookup(void *ctx, int type, int mat, const double *E, long long n, double *out, void *stream) {
+  if (!ctx || type < 0 || type > 2 || n < 0 || (n > 0 && (!E || !out))) return GV_ERR_BAD_ARG;
+  if (mat < 0 || mat >= ctx_nmat(ctx)) return GV_ERR_BAD_ARG;
+  if (n == 0) return GV_OK;
+  GV_UNIT_DISPATCH((k_lookup<float><<<blocks_for(n), kThreads, 0, s>>>(vf, type, mat, E, n, out)),
+                   (k_lookup<double><<<blocks_for(n), kThreads, 0, s>>>(vd, type, mat, E, n, out)))
+}
+
+int gv_unit_eloss(void *ctx, int type, int mat, const double *E, const double *sv, long long n, double *out,
+                  void *stream) {
+  if (!ctx || type < 1 || type > 2 || n < 0 || (n > 0 && (!E || !sv || !out))) return GV_ERR_BAD_ARG;
+  if (mat < 0 || mat >= ctx_nmat(ctx)) return GV_ERR_BAD_ARG;
+  if (n == 0) return GV_OK;
+  GV_UNIT_DISPATCH((k_eloss<float><<<blocks_for(n), kThreads, 0, s>>>(vf, type, mat, E, sv, n, out)),
+                   (k_eloss<double><<<blocks_for(n), kThreads, 0, s>>>(vd, type, mat, E, sv, n, out)))
+}
+
+int gv_unit_alias_sample(void *ctx, int model, const double *E, const double *u, long long n, double *out,
+                         void *stream) {
+  if (!ctx || model < 0 || model >= kNModel || n < 0 || (n > 0 && (!E || !u || !out))) return GV_ERR_BAD_ARG;
+  if (n == 0) return GV_OK;
+  GV_UNIT_DISPATCH((k_alias<float><<<blocks_for(n), kThreads, 0, s>>>(vf, model, E, u, n, out)),
+                   (k_alias<double><<<blocks_for(n), kThreads, 0, s>>>(vd, model, E, u, n, out)))
+}
+
+int gv_unit_interact(void *ctx, int type, int proc, const double *E, const double *dir, const double *u, long long n,
+                     double *out, int *ret, void *stream) {
+  if (!ctx || type < 0 || type > 2 || proc < 0 || proc > (type == 1 ? 1 : 2) || n < 0 ||
+      (n > 0 && (!E || !dir || !u || !out || !ret)))
+    return GV_ERR_BAD_ARG;
+  if (n == 0) return GV_OK;
+  GV_UNIT_DISPATCH((k_interact<float><<<blocks_for(n), kThreads, 0, s>>>(vf, type, proc, E, dir, u, n, out, ret)),
+                   (k_interact<double><<<blocks_for(n), kThreads, 0, s>>>(vd, type, proc, E, dir, u, n, out, ret)))
+}
+
+int gv_unit_distance(void *ctx, const double *pos, const double *dir, const int *sub, long long n, double *dist,
+                     int *next, int *plane, void *stream) {
+  if (!ctx || n < 0 || (n > 0 && (!pos || !dir || !sub || !dist || !next || !plane))) return GV_ERR_BAD_ARG;
+  if (n == 0) return GV_OK;
+  GV_UNIT_DISPATCH((k_distance<float><<<blocks_for(n), kThreads, 0, s>>>(vf, pos, dir, sub, n, dist, next, plane)),
+                   (k_distance<double><<<blocks_for(n), kThreads, 0, s>>>(vd, pos, dir, sub, n, dist, next, plane)))
+}
+
+}  // extern "C"

@@ -1,0 +1,243 @@
+"""Whole-shower parity of the CUDA transport with the FP64 oracle.
+
+FP64 mode: the GPU and the oracle draw the same Philox numbers for the same
+track step, so their histories coincide event by event unless rounding
+flips a branch; integer counts and deposits are compared per event.
+Mixed mode (FP32 physics, FP64 positions): per-layer mean deposits must agree
+within 3 combined standard errors on every layer, and within 0.5% on layers
+holding >= 1% of the deposit wherever the statistics resolve 0.5% at 3 sigma.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2005_00949_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+ME = 0.51099895
+NTHR = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module")
+def gvmod():
+    import torch
+    assert torch.cuda.is_available()
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2005_00949_gb300 import gv
+    return gv
+
+
+def _ctx(gv, wl, **kw):
+    kw.setdefault("stack_capacity", 1 << 22)
+    return gv.Context(wl, gv.gv_default_config(**kw))
+
+
+def _T0(wl):
+    t = np.zeros(wl.n_events)
+    np.add.at(t, wl.primaries["event"], wl.primaries["E"])
+    return t
+
+
+def layer_parity(wl, g_edep, o_edep, frac=0.01, rel=0.005):
+    """c23 criteria on per-layer means; returns the worst pull and rel diff."""
+    n = wl.n_events
+    g = g_edep.reshape(n, wl.n_layers, -1).sum(2)
+    o = o_edep.reshape(n, wl.n_layers, -1).sum(2)
+    mg, mo = g.mean(0), o.mean(0)
+    comb = np.sqrt(g.var(0, ddof=1) / n + o.var(0, ddof=1) / n)
+    live = comb > 0
+    pull = np.zeros_like(mg)
+    pull[live] = np.abs(mg - mo)[live] / comb[live]
+    assert pull.max() <= 3.0, (pull.max(), int(np.argmax(pull)))
+    big = (mo >= frac * mo.sum()) & (3 * comb <= rel * mo)
+    if big.any():
+        assert (np.abs(mg - mo)[big] <= rel * mo[big]).all()
+    # per-material totals
+    gm = g_edep.reshape(n, wl.n_layers, -1).sum(1)
+    om = o_edep.reshape(n, wl.n_layers, -1).sum(1)
+    cm = np.sqrt(gm.var(0, ddof=1) / n + om.var(0, ddof=1) / n)
+    assert (np.abs(gm.mean(0) - om.mean(0)) <= 3 * cm + 1e-12).all()
+    return pull.max(), big.sum()
+
+
+# ---------------------------------------------------------------- photon slab (config 1)
+@pytest.mark.parametrize("prec", [0, 1], ids=["mixed", "fp64"])
+def test_photon_slab_transmission(gvmod, oracle_mod, prec):
+    wl = W.photon_slab(100_000)
+    ctx = _ctx(gvmod, wl, precision=prec, per_event_counts=1)
+    r = ctx.transport(per_event=True)
+    assert r["status"] == 0
+    f = r["counters"]["unscattered"] / wl.n_events
+    o = oracle_mod.Oracle(wl)
+    mu = o.xs(0, 0, 0, 1.0) + o.xs(0, 1, 0, 1.0)
+    T = math.exp(-mu * 10.0)
+    assert abs(f - T) < 3 * math.sqrt(T * (1 - T) / wl.n_events)
+    ref = o.transport(n_threads=NTHR)
+    same = np.all(r["counts"][:, :11] == ref["counts"][:, :11], axis=1)
+    if prec == 1:
+        assert same.mean() > 0.999
+        assert np.allclose(r["edep"][same], ref["edep"][same], rtol=0, atol=1e-9)
+    else:
+        assert same.mean() > 0.99
+    tot = r["edep"].sum() + r["escape"].sum()
+    assert abs(tot / wl.n_events - 1.0) < 1e-6
+
+
+# ---------------------------------------------------------------- FP64 event-by-event
+def test_fp64_showers_follow_oracle_event_by_event(gvmod, oracle_mod):
+    wl = W.pbps_electrons(300, 1000.0)
+    ctx = _ctx(gvmod, wl, precision=1, per_event_counts=1)
+    r = ctx.transport(per_event=True)
+    assert r["status"] == 0
+    ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
+    same = np.all(r["counts"][:, :11] == ref["counts"][:, :11], axis=1)
+    assert same.mean() >= 0.9, same.mean()
+    assert np.abs(r["edep"][same] - ref["edep"][same]).max() < 1e-9 * 1000.0
+    assert np.abs(r["escape"][same] - ref["escape"][same]).max() < 1e-9 * 1000.0
+
+
+# ---------------------------------------------------------------- mixed statistical parity
+def test_mixed_showers_statistical_parity_1GeV(gvmod, oracle_mod):
+    wl = W.pbps_electrons(40_000, 1000.0)
+    ctx = _ctx(gvmod, wl)
+    r = ctx.transport()
+    assert r["status"] == 0
+    ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
+    pull, nbig = layer_parity(wl, r["edep"], ref["edep"])
+    assert nbig >= 5  # the 0.5% criterion is exercised on the layers near the maximum
+    steps_g = r["counters"]["steps"]
+    steps_o = ref["counts"][:, 0].sum()
+    assert abs(steps_g / steps_o - 1) < 0.01
+
+
+def test_energy_and_charge_conservation_mixed(gvmod):
+    wl = W.pbps_electrons(2000, 10_000.0)
+    ctx = _ctx(gvmod, wl, per_event_counts=1)
+    r = ctx.transport(per_event=True)
+    assert r["status"] == 0
+    c = r["counts"]
+    T0 = _T0(wl)
+    resid = (r["edep"].sum(1) + r["escape"] - (T0 + 2 * ME * (c[:, 8] - c[:, 7]))) / T0
+    assert np.abs(resid).max() < 1e-5, np.abs(resid).max()
+    assert np.all(c[:, 7] == c[:, 8] + c[:, 9])  # pairs = annihilations + escaped e+
+
+
+# ---------------------------------------------------------------- full-size workloads
+def test_full_size_pbps_10GeV_matches_oracle(gvmod, oracle_mod):
+    """The benchmark workload (2000 x 10 GeV e-) in the benchmark launch shape."""
+    wl = W.config(4)
+    ctx = _ctx(gvmod, wl, stack_capacity=1 << 23)
+    r = ctx.transport()
+    assert r["status"] == 0
+    ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
+    layer_parity(wl, r["edep"], ref["edep"])
+    tot = r["edep"].sum() + r["escape"].sum()
+    c = r["counters"]
+    assert abs(tot - (_T0(wl).sum() + 2 * ME * (c["n_annih"] - c["n_pair"]))) < 1e-6 * _T0(wl).sum()
+
+
+def test_mixed_types_config3(gvmod, oracle_mod):
+    wl = W.config(3)
+    ctx = _ctx(gvmod, wl, stack_capacity=1 << 23)
+    r = ctx.transport()
+    assert r["status"] == 0
+    sub = wl.subset(1024)
+    ref = oracle_mod.Oracle(sub).transport(n_threads=NTHR)
+    # events are independent: the first 1024 GPU events against the oracle's
+    layer_parity(sub, r["edep"][:1024], ref["edep"])
+    c = r["counters"]
+    T0 = _T0(wl).sum()
+    tot = r["edep"].sum() + r["escape"].sum()
+    assert abs(tot - (T0 + 2 * ME * (c["n_annih"] - c["n_pair"]))) < 1e-6 * T0
+
+
+def test_wsi_cells_subset(gvmod, oracle_mod):
+    wl = W.wsi_cells(300, 100_000.0)
+    ctx = _ctx(gvmod, wl, stack_capacity=1 << 23)
+    r = ctx.transport()
+    assert r["status"] == 0
+    per_layer_edep = r["edep"].reshape(300, 50, 2).sum((0, 2))
+    assert np.allclose(r["cell"].sum((1, 2)), per_layer_edep, rtol=1e-9)
+    ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
+    layer_parity(wl, r["edep"], ref["edep"])
+    # central cells: the 4x4 entry region carries most of the deposit on both sides
+    gc, oc = r["cell"][:, 14:18, 14:18].sum(), ref["cell"][:, 14:18, 14:18].sum()
+    assert abs(gc / oc - 1) < 0.01
+
+
+# ---------------------------------------------------------------- reproducibility
+def test_integer_counts_invariant_to_launch_shape(gvmod):
+    wl = W.pbps_mixed(120).subset(120)
+    wl.primaries["E"] = np.minimum(wl.primaries["E"], 5000.0)
+    base = None
+    shapes = [dict(block_size=256, steps_per_claim=4), dict(block_size=128, steps_per_claim=1),
+              dict(block_size=512, steps_per_claim=16, refill_batch=7, refill_low_water=1000),
+              dict(block_size=64, tail_steps_per_claim=1, tail_threshold=1 << 40),
+              dict(mode=1)]
+    for kw in shapes:
+        ctx = _ctx(gvmod, wl, per_event_counts=1, **kw)
+        r = ctx.transport(per_event=True)
+        assert r["status"] == 0
+        if base is None:
+            base = r
+            continue
+        assert np.array_equal(r["counts"][:, :11], base["counts"][:, :11]), kw
+        assert np.allclose(r["edep"], base["edep"], rtol=1e-6, atol=1e-9)
+        ctx.close()
+
+
+# ---------------------------------------------------------------- edge cases and failures
+def test_edge_cases(gvmod):
+    wl = W.pbps_electrons(4, 100.0)
+    ctx = _ctx(gvmod, wl, per_event_counts=1)
+    p = W.make_primaries(4)
+    p["w"] = 1.0
+    p["event"] = [0, 1, 2, 3]
+    p["type"] = [1, 2, 0, 1]
+    p["E"] = [50.0, 5e-4, 10.0, 30.0]
+    p["z"] = [0.0, 3.0, 0.0, -1.0]  # the last one starts outside the box
+    e = dict(wl.__dict__)
+    e.update(primaries=p)
+    r = ctx.transport(W.Workload(**e), per_event=True)
+    assert r["status"] == 0
+    assert r["escape"][3] == 30.0 and r["edep"][3].sum() == 0.0
+    # a positron below the tracking cut deposits its energy and annihilates at rest
+    assert r["counts"][1, 8] == 1 and r["counts"][1, 4] == 2
+    tot = r["edep"].sum(1) + r["escape"]
+    c = r["counts"]
+    assert np.allclose(tot, p["E"] + 2 * ME * (c[:, 8] - c[:, 7]), rtol=1e-6)
+    # no primaries at all
+    e.update(primaries=W.make_primaries(0), n_events=2)
+    r = ctx.transport(W.Workload(**e))
+    assert r["status"] == 0 and r["edep"].sum() == 0.0
+
+
+def test_failure_statuses_are_reported_without_hanging(gvmod):
+    wl = W.pbps_electrons(50, 10_000.0)
+    ctx = _ctx(gvmod, wl, stack_capacity=2048)
+    with pytest.raises(gvmod.GvError, match="overflow"):
+        ctx.transport()
+    assert ctx.last_result.status == -4
+    ctx2 = _ctx(gvmod, wl, max_generations=3)
+    with pytest.raises(gvmod.GvError, match="budget"):
+        ctx2.transport()
+    # the contexts stay usable after an error
+    small = W.pbps_electrons(2, 100.0)
+    assert ctx.transport(small)["status"] == 0
+
+
+def test_host_buffers_give_device_results(gvmod):
+    import torch
+    wl = W.pbps_electrons(64, 1000.0)
+    ctx = _ctx(gvmod, wl)
+    dev = ctx.transport()
+    edep = np.zeros((wl.n_events, 100))
+    esc = np.zeros(wl.n_events)
+    res = ctx.gv_transport(wl.primaries, wl.n_events, wl.seed, edep, None, esc)
+    assert res.status == 0
+    torch.cuda.synchronize()
+    assert np.allclose(edep, dev["edep"], rtol=1e-6, atol=1e-9)
+    assert res.counters[0] == dev["counters"]["steps"]

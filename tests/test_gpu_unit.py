@@ -1,0 +1,239 @@
+"""Element-wise parity of the CUDA device functions with the FP64 oracle.
+
+Same inputs and the same uniforms go to both sides through the C ABI; the
+bar is |gpu - oracle| <= tol * max(|oracle|, scale) with tol = 1e-5 in the
+mixed (FP32) mode and 1e-9 in the FP64 mode.  Where floating point decides a
+discrete branch (alias acceptance, grid energy, kinematic thresholds) samples
+within rounding distance of the decision are set aside and their fraction is
+bounded.  Sizes are ragged multiples of the 256-thread launch.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2005_00949_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+N = 100_003  # 391 blocks of 256 threads and a ragged tail
+TOL = {0: 1e-5, 1: 1e-9}
+ME = 0.51099895
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def gvmod():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2005_00949_gb300 import gv
+    return gv
+
+
+@pytest.fixture(scope="module")
+def oracle_pbps(oracle_mod):
+    return oracle_mod.Oracle(W.pbps_electrons(1))
+
+
+@pytest.fixture(scope="module", params=[0, 1], ids=["mixed", "fp64"])
+def ctx(request, gvmod):
+    c = gvmod.Context(W.pbps_electrons(1), gvmod.gv_default_config(precision=request.param,
+                                                                  stack_capacity=1 << 12))
+    c.prec = request.param
+    yield c
+    c.close()
+
+
+def _u24(rng, shape):
+    return rng.integers(1, 2 ** 24 + 1, size=shape).astype(np.float64) / 2.0 ** 24
+
+
+def _dev(torch, a, dtype=None):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda") if dtype is None else \
+        torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype=dtype)
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_bit_exact(torch, gvmod, oracle_mod):
+    rng = np.random.default_rng(11)
+    ctr = rng.integers(0, 2 ** 32, size=(N, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, size=(N, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = [0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344]
+    key[0] = [0xa4093822, 0x299f31d0]
+    c = _dev(torch, ctr.view(np.int32))
+    k = _dev(torch, key.view(np.int32))
+    o = torch.zeros((N, 4), dtype=torch.int32, device="cuda")
+    gvmod.gv_unit_philox(c, k, o)
+    got = o.cpu().numpy().view(np.uint32)
+    assert got[0].tolist() == [0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1]
+    idx = np.random.default_rng(1).choice(N, 4000, replace=False)
+    for i in idx:
+        assert got[i].tolist() == oracle_mod.philox4x32_10(ctr[i], key[i]).tolist()
+
+
+# ---------------------------------------------------------------- tables
+@pytest.mark.parametrize("ptype", [0, 1, 2])
+def test_xs_lookup_matches_oracle(torch, ctx, oracle_pbps, ptype):
+    rng = np.random.default_rng(20 + ptype)
+    E = 10 ** rng.uniform(-3.0, 6.0, N)
+    E[:289] = oracle_pbps.grid()  # every node exactly
+    E[289:292] = [1e-3, 1e6, 2e6]  # ends and beyond the grid
+    Ed = _dev(torch, E)
+    out = torch.zeros((N, 4), dtype=torch.float64, device="cuda")
+    nq = {0: 3, 1: 3, 2: 4}[ptype]
+    for mat in (0, 1):
+        ctx.gv_unit_xs_lookup(ptype, mat, Ed, out)
+        got = out.cpu().numpy()
+        sel = np.random.default_rng(3).choice(N, 6000, replace=False)
+        sel = np.concatenate([np.arange(292), sel])
+        for q in range(nq):
+            ref = oracle_pbps.lookup(ptype, q, mat, E[sel])
+            scale = 1e-7 * np.abs(oracle_pbps.table_nodes(ptype, q, mat)).max()
+            err = np.abs(got[sel, q] - ref) / np.maximum(np.abs(ref), scale)
+            assert err.max() < TOL[ctx.prec], (ptype, mat, q, err.max(), E[sel][np.argmax(err)])
+
+
+@pytest.mark.parametrize("ptype", [1, 2])
+def test_continuous_loss_matches_oracle(torch, ctx, oracle_pbps, ptype):
+    rng = np.random.default_rng(30 + ptype)
+    n = 20_011
+    E = 10 ** rng.uniform(-2.7, 5.0, n)
+    qR = 2 if ptype == 1 else 3
+    for mat in (0, 1):
+        R = oracle_pbps.lookup(ptype, qR, mat, E)
+        s = R * 10 ** rng.uniform(-4.5, 0.1, n)
+        out = torch.zeros(n, dtype=torch.float64, device="cuda")
+        ctx.gv_unit_eloss(ptype, mat, _dev(torch, E), _dev(torch, s), out)
+        got = out.cpu().numpy()
+        ref = oracle_pbps.eloss(ptype, mat, E, s)
+        err = np.abs(got - ref) / E
+        assert err.max() < TOL[ctx.prec], (mat, err.max(), E[np.argmax(err)], s[np.argmax(err)])
+
+
+# ---------------------------------------------------------------- alias sampling
+MODEL_RANGE = {0: (1e-3, 1e6), 1: (1.03, 1e6), 2: (1.0, 1e6), 3: (2.0, 1e6), 4: (1.0, 1e6), 5: (1e-3, 1e6)}
+
+
+def _knife_edge_mask(oracle_pbps, model, E, u):
+    """True where a discrete decision sits within rounding distance of its edge."""
+    E_lo, nE = oracle_pbps.alias_info(model)
+    l = np.log(E / E_lo) / (math.log(10) / 8)
+    frac = l - np.floor(l)
+    near = (np.abs(l - np.round(l)) < 1e-4) | (np.abs(u[:, 0] - frac) < 1e-4)
+    return near
+
+
+@pytest.mark.parametrize("model", range(6))
+def test_alias_sampling_matches_oracle(torch, ctx, oracle_pbps, model):
+    rng = np.random.default_rng(40 + model)
+    n = 30_011
+    lo, hi = MODEL_RANGE[model]
+    E = 10 ** rng.uniform(math.log10(lo) + 1e-3, math.log10(hi) + 0.3, n)
+    u = _u24(rng, (n, 3))
+    out = torch.zeros((n, 2), dtype=torch.float64, device="cuda")
+    ctx.gv_unit_alias_sample(model, _dev(torch, E), _dev(torch, u), out)
+    got = out.cpu().numpy()
+    ref, xi = oracle_pbps.alias_sample(model, E, u)
+    skip = _knife_edge_mask(oracle_pbps, model, E, u)
+    assert skip.mean() < 0.01
+    ok = ~skip
+    err = np.abs(got[ok, 0] - ref[ok]) / np.abs(ref[ok])
+    assert err.max() < TOL[ctx.prec], (model, err.max(), E[ok][np.argmax(err)])
+    assert np.abs(got[ok, 1] - xi[ok]).max() < TOL[ctx.prec]
+
+
+# ---------------------------------------------------------------- final states
+CASES = [(0, 0, (1e-3, 1e5)), (0, 1, (1e-3, 10.0)), (0, 2, (1.03, 1e5)),
+         (1, 0, (1.0, 1e5)), (1, 1, (2.0, 1e5)), (2, 0, (1.0, 1e5)), (2, 1, (1.0, 1e5)),
+         (2, 2, (1e-3, 1e5))]
+PROC_MODEL = {(0, 0): 0, (0, 2): 1, (1, 0): 2, (2, 0): 2, (1, 1): 3, (2, 1): 4, (2, 2): 5}
+
+
+@pytest.mark.parametrize("ptype,proc,rng_E", CASES)
+def test_interaction_matches_oracle(torch, ctx, oracle_pbps, ptype, proc, rng_E):
+    rng = np.random.default_rng(50 + 3 * ptype + proc)
+    n = 4_099
+    E = 10 ** rng.uniform(math.log10(rng_E[0]), math.log10(rng_E[1]), n)
+    c = rng.uniform(-1, 1, n)
+    ph = rng.uniform(0, 2 * math.pi, n)
+    d = np.stack([np.sqrt(1 - c * c) * np.cos(ph), np.sqrt(1 - c * c) * np.sin(ph), c], 1)
+    d[:10] = [0, 0, 1]
+    u = _u24(rng, (n, 8))
+    out = torch.zeros((n, 24), dtype=torch.float64, device="cuda")
+    ret = torch.zeros(n, dtype=torch.int32, device="cuda")
+    ctx.gv_unit_interact(ptype, proc, _dev(torch, E), _dev(torch, d), _dev(torch, u), out, ret)
+    got = out.cpu().numpy()
+    gret = ret.cpu().numpy()
+    tol = TOL[ctx.prec]
+    model = PROC_MODEL.get((ptype, proc))
+    skip = np.zeros(n, bool)
+    if model is not None:
+        skip |= _knife_edge_mask(oracle_pbps, model, E, u[:, 2:5])
+    checked = 0
+    for i in range(n):
+        r, o = oracle_pbps.interact(ptype, proc, E[i], d[i], u[i])
+        # a secondary at its production threshold may go either way
+        if any(abs(o[7 + 5 * j] - 1.0) < 1e-5 * E[i] for j in range(int(o[5]))) or \
+                abs(o[4] - 1.0) < 1e-5 * E[i]:
+            skip[i] = True
+        if skip[i]:
+            continue
+        checked += 1
+        g = got[i]
+        assert gret[i] == r, (i, E[i], gret[i], r)
+        assert int(g[5]) == int(o[5]), (i, E[i])
+        scale = E[i] + 2 * ME
+        assert abs(g[0] - o[0]) <= tol * scale, (i, E[i], g[0], o[0])
+        assert abs(g[4] - o[4]) <= tol * scale
+        if r == 1:  # primary momentum direction, weighted by its energy
+            assert np.abs(g[0] * g[1:4] - o[0] * o[1:4]).max() <= 10 * tol * scale, (i, E[i])
+        for j in range(int(o[5])):
+            b = 6 + 5 * j
+            assert int(g[b]) == int(o[b])
+            assert abs(g[b + 1] - o[b + 1]) <= tol * scale
+            assert np.abs(g[b + 1] * g[b + 2:b + 5] - o[b + 1] * o[b + 2:b + 5]).max() <= 10 * tol * scale, (i, j, E[i])
+    assert checked > 0.98 * n
+
+
+# ---------------------------------------------------------------- navigator
+def test_distance_matches_oracle(torch, ctx, oracle_pbps):
+    rng = np.random.default_rng(60)
+    nsub = oracle_pbps.n_subtotal()
+    zb = np.array([oracle_pbps.plane_z(k) for k in range(nsub + 1)])
+    sub = rng.integers(0, nsub, N).astype(np.int32)
+    pos = np.stack([rng.uniform(-20, 20, N), rng.uniform(-20, 20, N),
+                    zb[sub] + rng.uniform(0, 1, N) * (zb[sub + 1] - zb[sub])], 1)
+    pos[:50, 2] = zb[sub[:50]]  # on the lower plane
+    c = rng.uniform(-1, 1, N)
+    ph = rng.uniform(0, 2 * math.pi, N)
+    d = np.stack([np.sqrt(1 - c * c) * np.cos(ph), np.sqrt(1 - c * c) * np.sin(ph), c], 1)
+    d[50:60] = [0, 0, 1]
+    d[60:70] = [1, 0, 0]
+    sub[70] = -1  # not a sub-slab
+    dist = torch.zeros(N, dtype=torch.float64, device="cuda")
+    nxt = torch.zeros(N, dtype=torch.int32, device="cuda")
+    pl = torch.zeros(N, dtype=torch.int32, device="cuda")
+    ctx.gv_unit_distance(_dev(torch, pos), _dev(torch, d), _dev(torch, sub), dist, nxt, pl)
+    gd, gn, gp = dist.cpu().numpy(), nxt.cpu().numpy(), pl.cpu().numpy()
+    assert gd[70] == -1.0 and gn[70] == -1
+    tol = TOL[ctx.prec]
+    sel = np.concatenate([np.arange(70), np.random.default_rng(2).choice(np.arange(71, N), 8000, False)])
+    for i in sel:
+        s, nx, p = oracle_pbps.distance(pos[i], d[i], int(sub[i]))
+        assert abs(gd[i] - s) <= tol * max(s, 0.05), (i, gd[i], s)
+        # the exit face is unique unless two faces are within rounding of each other
+        if (gn[i], gp[i]) != (nx, p):
+            alt = []
+            for k in (0, 1):
+                if d[i][k] != 0:
+                    alt.append(((20 if d[i][k] > 0 else -20) - pos[i][k]) / d[i][k])
+            if d[i][2] != 0:
+                alt.append(((zb[sub[i] + 1] if d[i][2] > 0 else zb[sub[i]]) - pos[i][2]) / d[i][2])
+            alt = sorted(alt)
+            assert len(alt) > 1 and alt[1] - alt[0] <= 1e-5 * max(alt[0], 0.05), (i, gn[i], nx)

@@ -109,6 +109,7 @@ typedef struct {
   long long max_generations;  /* budget; exceeded -> GV_ERR_TIMEOUT */
   int per_event_counts;       /* 1: keep GV_NCOUNT counters per event (slower) */
   int process_sort;           /* 1: re-basket interacting tracks by process in each block */
+  long long max_events_in_flight; /* refill only while fewer events are unfinished (0: no cap) */
 } gv_config;
 
 /* A primary track; layout shared with the seeded input generator. */

@@ -15,6 +15,8 @@ __device__ __forceinline__ float m_log(float x) { return logf(x); }
 __device__ __forceinline__ double m_log(double x) { return log(x); }
 __device__ __forceinline__ float m_log1p(float x) { return log1pf(x); }
 __device__ __forceinline__ double m_log1p(double x) { return log1p(x); }
+__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
 __device__ __forceinline__ float m_exp(float x) { return expf(x); }
 __device__ __forceinline__ double m_exp(double x) { return exp(x); }
 __device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
@@ -53,6 +55,7 @@ struct CutConst {
 // Read-only view of everything one step needs.
 template <typename R> struct View {
   const V4<R> *xs;           // [(mat*3 + type)*kGridN + node], smem or global
+  const float *inv_node;     // 1/E_i of the grid nodes (FP32 lookups)
   const double *zb;          // nsub+1 planes
   const unsigned char *smat; // material of each sub-slab
   const AliasBin<R> *bins;   // all models, [off + ie*kNB + j]
@@ -83,12 +86,36 @@ template <typename R> __device__ __forceinline__ R u24(uint32_t x) {
 }
 
 // ---------------------------------------------------------------- tables
-template <typename R> __device__ __forceinline__ void grid_pos(R E, int &i, R &f) {
-  const R l = (m_log(E) - static_cast<R>(-6.907755278982137)) * static_cast<R>(kGridPerDecade / 2.302585092994046);
-  int k = static_cast<int>(m_floor(l));
+// Node interval i and fraction f of ln E between nodes i and i+1 (clamped).
+// FP64: directly from ln E.  FP32: ln E near 10 GeV carries ~1e-6 absolute
+// error, i.e. 1e-5 of a node interval, so the node comes from a coarse log2
+// and the fraction from log1p(E/E_i - 1), accurate to ~1e-6 of an interval.
+template <typename R> __device__ __forceinline__ void grid_pos(const View<R> &V, R E, int &i, R &f);
+
+template <> __device__ __forceinline__ void grid_pos<double>(const View<double> &, double E, int &i, double &f) {
+  const double l = (log(E) + 6.907755278982137) * (kGridPerDecade / 2.302585092994046);
+  int k = static_cast<int>(floor(l));
   k = k < 0 ? 0 : (k > kGridN - 2 ? kGridN - 2 : k);
-  R fr = l - static_cast<R>(k);
-  fr = fr < R(0) ? R(0) : (fr > R(1) ? R(1) : fr);
+  double fr = l - static_cast<double>(k);
+  fr = fr < 0.0 ? 0.0 : (fr > 1.0 ? 1.0 : fr);
+  i = k;
+  f = fr;
+}
+
+template <> __device__ __forceinline__ void grid_pos<float>(const View<float> &V, float E, int &i, float &f) {
+  constexpr float kInvDl = static_cast<float>(kGridPerDecade / 2.302585092994046);
+  const float l = (__log2f(E) + 9.965784284662087f) * 9.632959861247398f;
+  int k = __float2int_rd(l);
+  k = k < 0 ? 0 : (k > kGridN - 2 ? kGridN - 2 : k);
+  float fr = log1pf(fmaf(E, V.inv_node[k], -1.0f)) * kInvDl;
+  if (fr < 0.0f && k > 0) {
+    --k;
+    fr = log1pf(fmaf(E, V.inv_node[k], -1.0f)) * kInvDl;
+  } else if (fr >= 1.0f && k < kGridN - 2) {
+    ++k;
+    fr = log1pf(fmaf(E, V.inv_node[k], -1.0f)) * kInvDl;
+  }
+  fr = fr < 0.0f ? 0.0f : (fr > 1.0f ? 1.0f : fr);
   i = k;
   f = fr;
 }
@@ -105,7 +132,7 @@ template <typename R> __device__ __forceinline__ V4<R> lerp4(const V4<R> &a, con
 template <typename R> __device__ __forceinline__ V4<R> lookup(const View<R> &V, int mat, int type, R E) {
   int i;
   R f;
-  grid_pos(E, i, f);
+  grid_pos(V, E, i, f);
   const V4<R> *t = V.xs + (mat * 3 + type) * kGridN;
   return lerp4(t[i], t[i + 1], f);
 }
@@ -123,7 +150,7 @@ template <typename R> __device__ R eloss(const View<R> &V, int mat, int type, R 
   const V4<R> *t = V.xs + (mat * 3 + type) * kGridN;
   int i;
   R f;
-  grid_pos(E, i, f);
+  grid_pos(V, E, i, f);
   const R Ri = range_at(t[i], type), Rj = range_at(t[i + 1], type);
   const R dR = Rj - Ri;
   const R Rv = Ri + f * dR;
@@ -255,22 +282,23 @@ template <typename R> struct Kids {
   R d[3][3];
 };
 
-template <typename R> __device__ __forceinline__ void add_kid(Kids<R> &k, int type, R E, R a, R b, R c) {
-  const int n = k.n;
-  k.type[n] = type;
-  k.E[n] = E;
-  k.d[n][0] = a;
-  k.d[n][1] = b;
-  k.d[n][2] = c;
-  k.n = n + 1;
+template <typename R> __device__ __forceinline__ void add_kid(Kids<R> &k, int type, R E, const R d[3]) {
+  // fixed-index stores keep the arrays in registers
+  if (k.n == 0) {
+    k.type[0] = type; k.E[0] = E; k.d[0][0] = d[0]; k.d[0][1] = d[1]; k.d[0][2] = d[2];
+  } else if (k.n == 1) {
+    k.type[1] = type; k.E[1] = E; k.d[1][0] = d[0]; k.d[1][1] = d[1]; k.d[1][2] = d[2];
+  } else {
+    k.type[2] = type; k.E[2] = E; k.d[2][0] = d[0]; k.d[2][1] = d[1]; k.d[2][2] = d[2];
+  }
+  k.n += 1;
 }
 
-// rotate unit vector d by polar cosine ct and azimuth phi about itself
-template <typename R> __device__ __forceinline__ void rotate(const R d[3], R ct, R phi, R o[3]) {
-  R st = R(1) - ct * ct;
-  st = st > R(0) ? m_sqrt(st) : R(0);
-  R sp, cp;
-  m_sincos(phi, &sp, &cp);
+// Rotate unit vector d to polar angle (ct, st) and azimuth (cp, sp) about
+// itself (the frame of G4ThreeVector::rotateUz).  Callers pass st from a
+// cancellation-free expression so small angles survive in FP32.
+template <typename R>
+__device__ __forceinline__ void rotate(const R d[3], R ct, R st, R cp, R sp, R o[3]) {
   const R lx = st * cp, ly = st * sp, lz = ct;
   R up = d[0] * d[0] + d[1] * d[1];
   if (up > R(0)) {
@@ -285,48 +313,63 @@ template <typename R> __device__ __forceinline__ void rotate(const R d[3], R ct,
   }
 }
 
-template <typename R> __device__ __forceinline__ void unit_or(R a, R b, R c, const R fb[3], R o[3]) {
-  const R n2 = a * a + b * b + c * c;
-  if (n2 > R(0)) {
-    const R n = m_sqrt(n2);
-    o[0] = a / n; o[1] = b / n; o[2] = c / n;
-  } else {
-    o[0] = fb[0]; o[1] = fb[1]; o[2] = fb[2];
+// direction at polar components (along, perp) -- not normalised -- and azimuth
+template <typename R>
+__device__ __forceinline__ void rotate_vec(const R d[3], R along, R perp, R cp, R sp, R o[3]) {
+  const R n2 = along * along + perp * perp;
+  if (!(n2 > R(0))) {
+    o[0] = d[0]; o[1] = d[1]; o[2] = d[2];
+    return;
   }
+  const R inv = R(1) / m_sqrt(n2);
+  rotate(d, along * inv, perp * inv, cp, sp, o);
 }
 
 template <typename R> __device__ __forceinline__ void at_rest(Kids<R> &k, R u6, R u7) {
   const R ct = R(2) * u6 - R(1);
-  R st = R(1) - ct * ct;
-  st = st > R(0) ? m_sqrt(st) : R(0);
+  const R st = R(2) * m_sqrt(u6 * (R(1) - u6));
   R sp, cp;
   m_sincos(static_cast<R>(2.0 * kPi) * u7, &sp, &cp);
-  add_kid(k, 0, static_cast<R>(kME), st * cp, st * sp, ct);
-  add_kid(k, 0, static_cast<R>(kME), -(st * cp), -(st * sp), -ct);
+  const R a[3] = {st * cp, st * sp, ct};
+  const R b[3] = {-a[0], -a[1], -a[2]};
+  add_kid(k, 0, static_cast<R>(kME), a);
+  add_kid(k, 0, static_cast<R>(kME), b);
 }
 
 // Final state (PostStepActions) of process p.  u[2..7]: grid, bin, in-bin,
 // azimuth, isotropic pair.  Returns 1 survives, 0 ended, -1 not possible.
+// Angles use forms of 1 -+ cos(theta) that carry no cancellation, written
+// from the sampled reduced variable xi; they are algebraically the textbook
+// two-body kinematics.
 template <typename R>
 __device__ int interact(const View<R> &V, int type, int p, R &E, R d[3], const R *u, Kids<R> &kids, R &local,
                         int &npair, int &nann) {
   const R ME = static_cast<R>(kME);
   const R ecut_push = static_cast<R>(V.cut.ecut > V.cut.tcut ? V.cut.ecut : V.cut.tcut);
   const R tcut = static_cast<R>(V.cut.tcut);
-  const R phi = static_cast<R>(2.0 * kPi) * u[5];
+  R sp, cp;
+  m_sincos(static_cast<R>(2.0 * kPi) * u[5], &sp, &cp);
   local = R(0);
+  R xi;
   if (type == 0) {
     const R k = E;
-    if (p == 0) {  // Compton
-      const R eps = alias_sample<R>(V, kCompton, k, u[2], u[3], u[4]);
-      R ct = R(1) - (R(1) - eps) * ME / (k * eps);
-      ct = ct < R(-1) ? R(-1) : (ct > R(1) ? R(1) : ct);
-      R d1[3];
-      rotate(d, ct, phi, d1);
-      const R k1 = eps * k, Te = k - k1;
-      R de[3];
-      unit_or(k * d[0] - k1 * d1[0], k * d[1] - k1 * d1[1], k * d[2] - k1 * d1[2], d, de);
-      if (Te >= ecut_push) add_kid(kids, 1, Te, de[0], de[1], de[2]);
+    if (p == 0) {  // Compton: eps = eps0^(1-xi)
+      (void)alias_sample<R>(V, kCompton, k, u[2], u[3], u[4], &xi);
+      const R kap = k / ME;
+      const R L0 = -m_log1p(R(2) * kap);
+      const R a = (R(1) - xi) * L0;
+      const R eps = m_exp(a);
+      const R om_eps = -m_expm1(a);                 // 1 - eps
+      const R omc = om_eps / (kap * eps);           // 1 - cos(theta)
+      const R opc = m_expm1(-xi * L0) / (kap * eps);  // 1 + cos(theta)
+      const R st = m_sqrt(omc * opc);
+      const R ct = omc < R(1) ? R(1) - omc : opc - R(1);
+      R d1[3], de[3];
+      rotate(d, ct, st, cp, sp, d1);
+      const R k1 = eps * k, Te = k * om_eps;
+      // electron momentum k d - k' d' = k [(1 - eps ct) d - eps st e_phi]
+      rotate_vec(d, om_eps + eps * omc, eps * st, -cp, -sp, de);
+      if (Te >= ecut_push) add_kid(kids, 1, Te, de);
       else local += Te;
       d[0] = d1[0]; d[1] = d1[1]; d[2] = d1[2];
       if (k1 < tcut) { local += k1; E = R(0); return 0; }
@@ -334,24 +377,25 @@ __device__ int interact(const View<R> &V, int type, int p, R &E, R d[3], const R
       return 1;
     }
     if (p == 1) {  // photoelectric
-      if (k >= ecut_push) add_kid(kids, 1, k, d[0], d[1], d[2]);
+      if (k >= ecut_push) add_kid(kids, 1, k, d);
       else local += k;
       E = R(0);
       return 0;
     }
     if (!(k > R(2) * ME)) return -1;  // pair
-    const R x = alias_sample<R>(V, kPair, k, u[2], u[3], u[4]);
+    const R x = alias_sample<R>(V, kPair, k, u[2], u[3], u[4], &xi);
     R Tm = x * k - ME, Tp = (R(1) - x) * k - ME;
     Tm = Tm < R(0) ? R(0) : Tm;
     Tp = Tp < R(0) ? R(0) : Tp;
-    const R ct = m_cos(ME / k);
+    R st, ct;
+    m_sincos(ME / k, &st, &ct);
     R dm[3], dp[3];
-    rotate(d, ct, phi, dm);
-    rotate(d, ct, phi + static_cast<R>(kPi), dp);
+    rotate(d, ct, st, cp, sp, dm);
+    rotate(d, ct, st, -cp, -sp, dp);
     npair += 1;
-    if (Tm >= ecut_push) add_kid(kids, 1, Tm, dm[0], dm[1], dm[2]);
+    if (Tm >= ecut_push) add_kid(kids, 1, Tm, dm);
     else local += Tm;
-    if (Tp >= ecut_push) add_kid(kids, 2, Tp, dp[0], dp[1], dp[2]);
+    if (Tp >= ecut_push) add_kid(kids, 2, Tp, dp);
     else {
       local += Tp;
       at_rest(kids, u[6], u[7]);
@@ -363,39 +407,52 @@ __device__ int interact(const View<R> &V, int type, int p, R &E, R d[3], const R
   R T = E;
   if (p == 0) {  // bremsstrahlung
     if (!(T > static_cast<R>(V.cut.gcut))) return -1;
-    const R kg = alias_sample<R>(V, kBrem, T, u[2], u[3], u[4]);
-    R dg[3];
-    rotate(d, m_cos(ME / (T + ME)), phi, dg);
-    if (kg >= tcut) add_kid(kids, 0, kg, dg[0], dg[1], dg[2]);
+    const R kg = alias_sample<R>(V, kBrem, T, u[2], u[3], u[4], &xi);
+    R st, ct, dg[3];
+    m_sincos(ME / (T + ME), &st, &ct);
+    rotate(d, ct, st, cp, sp, dg);
+    if (kg >= tcut) add_kid(kids, 0, kg, dg);
     else local += kg;
     T -= kg;
-  } else if (p == 1) {  // ionisation
+  } else if (p == 1) {  // ionisation: Moller eps = xc (1/(2xc))^xi, Bhabha eps = xc^(1-xi)
     const R ec = static_cast<R>(V.cut.ecut);
     if (type == 1 && !(T > R(2) * ec)) return -1;
     if (type == 2 && !(T > ec)) return -1;
-    const R eps = alias_sample<R>(V, type == 1 ? kMoller : kBhabha, T, u[2], u[3], u[4]);
+    const R eps = alias_sample<R>(V, type == 1 ? kMoller : kBhabha, T, u[2], u[3], u[4], &xi);
+    const R om_eps = type == 1 ? R(1) - eps : -m_expm1((R(1) - xi) * m_log(ec / T));
     const R Td = eps * T;
-    R ct = m_sqrt(Td * (T + R(2) * ME) / (T * (Td + R(2) * ME)));
-    ct = ct > R(1) ? R(1) : ct;
-    R dd[3];
-    rotate(d, ct, phi, dd);
-    const R P = m_sqrt(T * (T + R(2) * ME)), Pd = m_sqrt(Td * (Td + R(2) * ME));
-    R dn[3];
-    unit_or(P * d[0] - Pd * dd[0], P * d[1] - Pd * dd[1], P * d[2] - Pd * dd[2], d, dn);
-    add_kid(kids, 1, Td, dd[0], dd[1], dd[2]);
-    d[0] = dn[0]; d[1] = dn[1]; d[2] = dn[2];
-    T -= Td;
-  } else {  // annihilation in flight
-    const R eps = alias_sample<R>(V, kAnnih, T, u[2], u[3], u[4]);
-    const R tot = T + R(2) * ME, k1 = eps * tot, k2 = tot - k1;
+    const R den = eps * T + R(2) * ME;
+    // delta ray: cos^2 = eps (T + 2m) / (eps T + 2m), sin^2 = 2m (1 - eps) / (eps T + 2m)
+    const R ct = m_sqrt(eps * (T + R(2) * ME) / den), st = m_sqrt(R(2) * ME * om_eps / den);
+    R dd[3], dn[3];
+    rotate(d, ct, st, cp, sp, dd);
+    // primary: p' = p (1 - eps) along d, sqrt(2 m T eps (1 - eps)) across
     const R P = m_sqrt(T * (T + R(2) * ME));
-    R ct = (k1 - ME) / (eps * P);
-    ct = ct < R(-1) ? R(-1) : (ct > R(1) ? R(1) : ct);
+    rotate_vec(d, P * om_eps, m_sqrt(R(2) * ME * T * eps * om_eps), -cp, -sp, dn);
+    add_kid(kids, 1, Td, dd);
+    d[0] = dn[0]; d[1] = dn[1]; d[2] = dn[2];
+    T = T * om_eps;
+  } else {  // annihilation in flight: softer photon eps = eps_min (1/(2 eps_min))^xi
+    (void)alias_sample<R>(V, kAnnih, T, u[2], u[3], u[4], &xi);
+    const R t = T / ME;
+    const R s = m_sqrt(t / (t + R(2)));
+    const R emin = R(1) / ((t + R(2)) * (R(1) + s));
+    const R Lr = m_log(R(0.5) / emin);
+    const R eps = emin * m_exp(xi * Lr);
+    const R D = emin * m_expm1(xi * Lr);  // eps - eps_min
+    const R W = T + R(2) * ME, P = m_sqrt(T * (T + R(2) * ME)), Q = W + P;
+    const R k1 = eps * W, k2 = (R(1) - eps) * W;
+    // photon 1: 1 - cos = m (W (1 - 2 eps) + P) / (eps P Q), 1 + cos = D Q / (eps P)
+    const R omc1 = ME * (W * (R(1) - R(2) * eps) + P) / (eps * P * Q);
+    const R opc1 = D * Q / (eps * P);
+    // photon 2: 1 - cos = 2 m W D / ((1 - eps) P Q), 1 + cos = (s - D) Q / ((1 - eps) P)
+    const R omc2 = R(2) * ME * W * D / ((R(1) - eps) * P * Q);
+    const R opc2 = (s - D) * Q / ((R(1) - eps) * P);
     R d1[3], d2[3];
-    rotate(d, ct, phi, d1);
-    unit_or(P * d[0] - k1 * d1[0], P * d[1] - k1 * d1[1], P * d[2] - k1 * d1[2], d, d2);
-    add_kid(kids, 0, k1, d1[0], d1[1], d1[2]);
-    add_kid(kids, 0, k2, d2[0], d2[1], d2[2]);
+    rotate(d, omc1 < R(1) ? R(1) - omc1 : opc1 - R(1), m_sqrt(omc1 * opc1), cp, sp, d1);
+    rotate(d, omc2 < R(1) ? R(1) - omc2 : opc2 - R(1), m_sqrt(omc2 * opc2), -cp, -sp, d2);
+    add_kid(kids, 0, k1, d1);
+    add_kid(kids, 0, k2, d2);
     nann += 1;
     E = R(0);
     return 0;

@@ -16,6 +16,9 @@ template <typename R> struct Queue {
   int *sf;  // sub-slab | flags << 16
 };
 
+// reciprocal node energies staged in shared memory, padded to 16 bytes
+constexpr unsigned kInvNodeBytes = (kGridN * sizeof(float) + 15) / 16 * 16;
+
 constexpr int kFlagPrimary = 1;
 constexpr int kFlagInteracted = 2;
 
@@ -36,6 +39,7 @@ struct Ctl {
   int status;
   int done;
   int pad;
+  unsigned ev_started, ev_done;  // events whose live-track count left / returned to zero
   unsigned long long gen;
   unsigned long long live_peak;
   unsigned long long counters[16];
@@ -51,11 +55,14 @@ template <typename R> struct DevState {
   unsigned n_prim, n_events;
   double *edep, *cell, *escape;
   unsigned long long *evcnt;
+  unsigned *evlive;          // live tracks per event (events-in-flight accounting)
+  unsigned max_in_flight;    // 0: no cap
   unsigned seed_lo, seed_hi;
   int block_size, mode, K_bulk, K_tail;
   unsigned long long tail_threshold, low_water, batch, max_gen;
   int n_mat;
   unsigned xs_bytes, zb_bytes;  // staged into shared memory
+  unsigned smem_req_off;        // start of the basketizer's request records
 };
 
 }  // namespace gv

@@ -61,12 +61,16 @@ template <typename R> struct Trk {
 __device__ __forceinline__ void set_status(Ctl *ctl, int code) { atomicCAS(&ctl->status, 0, code); }
 
 // ------------------------------------------------------------------ one step
-// Returns 1 if the track is still alive.  Secondaries go to `kids`; kk is
-// the step index whose counter blocks derive the children's ids.
+// PreStep .. process choice of one step.  Returns 1 if the track is still
+// alive; then proc >= 0 names the discrete process due at the post-step
+// point and u[] holds the step's eight uniforms for its final state.
+// Secondaries made so far go to `kids`; kk is the step index whose counter
+// blocks derive the children's ids.
 template <typename R>
 __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kids<R> &kids, uint32_t &kk,
-                          BlockCnt *bc) {
+                          BlockCnt *bc, int &proc_out, R *u) {
   kids.n = 0;
+  proc_out = -1;
   const uint32_t k = t.step;
   kk = k;
   const uint32_t key0 = S->seed_lo ^ t.ev, key1 = S->seed_hi;
@@ -169,20 +173,27 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   t.nlam = R(-1);
   if (proc < 0) return 1;
   const uint4 r1 = philox4x32_10(make_uint4(idlo, idhi, k, 1u), key0, key1);
-  R u[8] = {u24<R>(r0.x), u24<R>(r0.y), u24<R>(r0.z), u24<R>(r0.w),
-            u24<R>(r1.x), u24<R>(r1.y), u24<R>(r1.z), u24<R>(r1.w)};
-  R d[3] = {t.u, t.v, t.w};
+  u[0] = u24<R>(r0.x); u[1] = u24<R>(r0.y); u[2] = u24<R>(r0.z); u[3] = u24<R>(r0.w);
+  u[4] = u24<R>(r1.x); u[5] = u24<R>(r1.y); u[6] = u24<R>(r1.z); u[7] = u24<R>(r1.w);
+  proc_out = proc;
+  return 1;
+}
+
+// PostStepActions of a track whose step ended in process `proc`: the final
+// state, the local deposit and the counters.  Returns 1 if the particle
+// survives, 0 if it ended, -1 if the process was kinematically closed at the
+// post-step energy (nothing changes).
+template <typename R>
+__device__ __forceinline__ int final_state(const View<R> &V, const DevState<R> *S, BlockCnt *bc, int type, int proc,
+                                           R &E, R d[3], const R *u, Kids<R> &kids, unsigned ev, int sub,
+                                           double x, double y) {
   R local;
   int np = 0, na = 0;
-  const int r = interact(V, t.type, proc, t.E, d, u, kids, local, np, na);
-  if (r < 0) return 1;
-  t.u = d[0];
-  t.v = d[1];
-  t.w = d[2];
-  t.flags |= kFlagInteracted;
-  if (np) count(S, bc, t.ev, GV_C_PAIR, np);
-  if (na) count(S, bc, t.ev, GV_C_ANNIH, na);
-  deposit(V, S, t.ev, t.sub, t.x, t.y, local);
+  const int r = interact(V, type, proc, E, d, u, kids, local, np, na);
+  if (r < 0) return -1;
+  if (np) count(S, bc, ev, GV_C_PAIR, np);
+  if (na) count(S, bc, ev, GV_C_ANNIH, na);
+  deposit(V, S, ev, sub, x, y, local);
   return r;
 }
 
@@ -222,13 +233,32 @@ __device__ __forceinline__ void store(const Queue<R> &q, unsigned slot, double x
   q.sf[slot] = sf;
 }
 
-// S9: append the step's secondaries to the output queues.
+// The parent of a step's secondaries: where they start and whose lineage
+// names them.
+struct Parent {
+  double x, y, z;
+  unsigned long long id;
+  unsigned ev;
+  int sub;
+};
+
+template <typename R> __device__ __forceinline__ Parent parent_of(const Trk<R> &t) {
+  Parent p;
+  p.x = t.x; p.y = t.y; p.z = t.z;
+  p.id = t.id;
+  p.ev = t.ev;
+  p.sub = t.sub;
+  return p;
+}
+
+// S9: append the step's secondaries to the output queues.  Called by all 32
+// lanes of a converged warp (lanes without secondaries pass kids.n == 0).
 template <typename R>
-__device__ void push_kids(const DevState<R> *S, int out, const Trk<R> &t, const Kids<R> &kids, uint32_t kk,
+__device__ void push_kids(const DevState<R> *S, int out, const Parent &t, const Kids<R> &kids, uint32_t kk,
                           BlockCnt *bc) {
   const unsigned any = __ballot_sync(0xffffffffu, kids.n > 0);
   if (!any) return;
-  uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  uint32_t w[6] = {0, 0, 0, 0, 0, 0};
   if (kids.n > 0) {
     const uint32_t key0 = S->seed_lo ^ t.ev;
     const uint4 a = philox4x32_10(make_uint4(static_cast<uint32_t>(t.id), static_cast<uint32_t>(t.id >> 32), kk, kTagId),
@@ -237,13 +267,14 @@ __device__ void push_kids(const DevState<R> *S, int out, const Trk<R> &t, const 
     if (kids.n > 2) {
       const uint4 b = philox4x32_10(
           make_uint4(static_cast<uint32_t>(t.id), static_cast<uint32_t>(t.id >> 32), kk, kTagId + 1u), key0, S->seed_hi);
-      w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+      w[4] = b.x; w[5] = b.y;
     }
   }
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     unsigned c = 0;
-    for (int j = 0; j < kids.n; ++j) c += kids.type[j] == q;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) c += (j < kids.n && kids.type[j] == q) ? 1u : 0u;
     if (!__ballot_sync(0xffffffffu, c > 0)) continue;
     unsigned total;
     unsigned slot = warp_reserve(&S->ctl->cnt[out][q], c, total);
@@ -253,8 +284,9 @@ __device__ void push_kids(const DevState<R> *S, int out, const Trk<R> &t, const 
       set_status(S->ctl, GV_ERR_STACK_FULL);
       continue;
     }
-    for (int j = 0; j < kids.n; ++j) {
-      if (kids.type[j] != q) continue;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      if (!(j < kids.n && kids.type[j] == q)) continue;
       const unsigned long long id = static_cast<unsigned long long>(w[2 * j]) |
                                     (static_cast<unsigned long long>(w[2 * j + 1]) << 32);
       store(S->q[out][q], slot, t.x, t.y, t.z, kids.d[j][0], kids.d[j][1], kids.d[j][2], kids.E[j], R(-1), id, t.ev,
@@ -263,7 +295,26 @@ __device__ void push_kids(const DevState<R> *S, int out, const Trk<R> &t, const 
       ++slot;
     }
   }
+  // the event's live-track count grows before the parent's own end is booked
+  if (kids.n > 0) atomicAdd(&S->evlive[t.ev], static_cast<unsigned>(kids.n));
 }
+
+// A track ended: book it against its event; the last one closes the event.
+template <typename R> __device__ __forceinline__ void track_ended(const DevState<R> *S, unsigned ev) {
+  if (atomicSub(&S->evlive[ev], 1u) == 1u) atomicAdd(&S->ctl->ev_done, 1u);
+}
+
+// An interaction request staged in shared memory by the in-block basketizer.
+template <typename R> struct IReq {
+  double x, y, z;
+  unsigned long long id;
+  R E, d0, d1, d2;
+  R u[6];      // u2..u7 of the step
+  unsigned ev, kk;
+  int sub;
+  int tp;      // in: type*3 + process; out: final_state's return code
+};
+constexpr int kNKey = 9;
 
 template <typename R>
 __device__ __forceinline__ void push_survivor(const DevState<R> *S, int out, const Trk<R> &t, bool alive) {
@@ -304,6 +355,11 @@ template <typename R> __device__ void plan_next(const DevState<R> *S, int pn) {
       }
     } else if (live < S->low_water || live == 0) {
       inj = rem < S->batch ? rem : static_cast<unsigned>(S->batch);
+      if (S->max_in_flight) {  // events in flight (Sec. 2.1.1): started and not yet finished
+        const unsigned fl = c->ev_started - c->ev_done;
+        const unsigned room = S->max_in_flight > fl ? S->max_in_flight - fl : 0u;
+        inj = inj < room ? inj : room;
+      }
     }
   }
   c->prim_begin = c->prim_next;
@@ -335,17 +391,22 @@ template <typename R> __global__ void init_kernel(const DevState<R> *S) {
   c->done = 0;
   c->gen = 0;
   c->live_peak = 0;
+  c->ev_started = 0;
+  c->ev_done = 0;
   for (int i = 0; i < 16; ++i) c->counters[i] = 0;
   plan_next(S, 0);
 }
 
 // ------------------------------------------------------------------ the kernel
-template <typename R> __global__ void __launch_bounds__(512) step_kernel(const DevState<R> *__restrict__ S, int parity) {
+template <typename R, bool SORT>
+__global__ void __launch_bounds__(512) step_kernel(const DevState<R> *__restrict__ S, int parity) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ View<R> sV;
   __shared__ BlockCnt bc;
   __shared__ unsigned s_chunk, s_end[4], s_pb;
   __shared__ int s_K, s_last;
+  __shared__ unsigned s_wcnt[SORT ? kNKey : 1][SORT ? 16 : 1];
+  __shared__ unsigned s_nreq;
   Ctl *ctl = S->ctl;
   const int tid = threadIdx.x;
   if (ctl->done) return;  // uniform: nothing planned for this generation
@@ -358,12 +419,15 @@ template <typename R> __global__ void __launch_bounds__(512) step_kernel(const D
     double *zdst = reinterpret_cast<double *>(smem + S->xs_bytes);
     const int nz = S->view.geo.nsub + 1;
     for (int i = tid; i < nz; i += blockDim.x) zdst[i] = zsrc[i];
-    unsigned char *mdst = smem + S->xs_bytes + S->zb_bytes;
+    float *idst = reinterpret_cast<float *>(smem + S->xs_bytes + S->zb_bytes);
+    for (int i = tid; i < kGridN; i += blockDim.x) idst[i] = S->view.inv_node[i];
+    unsigned char *mdst = smem + S->xs_bytes + S->zb_bytes + kInvNodeBytes;
     for (int i = tid; i < S->view.geo.nsub; i += blockDim.x) mdst[i] = S->view.smat[i];
     if (tid == 0) {
       sV = S->view;
       sV.xs = reinterpret_cast<const V4<R> *>(smem);
       sV.zb = zdst;
+      sV.inv_node = idst;
       sV.smat = mdst;
       for (int i = 0; i < 4; ++i) s_end[i] = ctl->chunk_end[i];
       s_pb = ctl->prim_begin;
@@ -429,22 +493,112 @@ template <typename R> __global__ void __launch_bounds__(512) step_kernel(const D
         if (t.type == 2) count(S, &bc, t.ev, GV_C_EP_ESC);
       } else {
         alive = true;
+        if (atomicAdd(&S->evlive[t.ev], 1u) == 0u) atomicAdd(&ctl->ev_started, 1u);
       }
     }
     const int K = s_K;
     for (int kk = 0; kk < K; ++kk) {
-      if (!__any_sync(0xffffffffu, alive)) break;
+      if (SORT) {
+        if (!__syncthreads_or(alive)) break;  // block-uniform: the basketizer syncs
+      } else if (!__any_sync(0xffffffffu, alive)) {
+        break;
+      }
+      const bool was_alive = alive;
       Kids<R> kids;
       kids.n = 0;
       uint32_t kstep = 0;
+      int proc = -1;
+      R u[8];
       if (alive) {
-        alive = step_track(V, S, t, kids, kstep, &bc) != 0;
+        alive = step_track(V, S, t, kids, kstep, &bc, proc, u) != 0;
         if (!(t.E == t.E) || !(t.z == t.z)) {
           set_status(ctl, GV_ERR_NUMERIC);
           alive = false;
+          proc = -1;
+        }
+        if (!SORT && proc >= 0) {  // final state in place (warp-divergent across processes)
+          R d[3] = {t.u, t.v, t.w};
+          const int r = final_state(V, S, &bc, t.type, proc, t.E, d, u, kids, t.ev, t.sub, t.x, t.y);
+          if (r >= 0) {
+            t.u = d[0]; t.v = d[1]; t.w = d[2];
+            t.flags |= kFlagInteracted;
+            alive = r != 0;
+          }
         }
       }
-      push_kids(S, out, t, kids, kstep, &bc);
+      push_kids(S, out, parent_of(t), kids, kstep, &bc);
+      if (SORT) {
+        // S1 basketizer: counting sort of this step's interaction requests by
+        // (type, process) -- warp ballots, a block prefix sum, one slot each --
+        // so every warp runs a single final-state model.
+        IReq<R> *req = reinterpret_cast<IReq<R> *>(smem + S->smem_req_off);
+        const int key = (alive && proc >= 0) ? t.type * 3 + proc : -1;
+        const int lane = tid & 31, warp = tid >> 5;
+        unsigned rank = 0;
+#pragma unroll
+        for (int k = 0; k < kNKey; ++k) {
+          const unsigned m = __ballot_sync(0xffffffffu, key == k);
+          if (lane == 0) s_wcnt[k][warp] = __popc(m);
+          if (key == k) rank = __popc(m & ((1u << lane) - 1u));
+        }
+        __syncthreads();
+        if (tid == 0) {
+          const int nw = blockDim.x >> 5;
+          unsigned run = 0;
+          for (int k = 0; k < kNKey; ++k)
+            for (int w = 0; w < nw; ++w) {
+              const unsigned c = s_wcnt[k][w];
+              s_wcnt[k][w] = run;
+              run += c;
+            }
+          s_nreq = run;
+        }
+        __syncthreads();
+        const unsigned slot = key >= 0 ? s_wcnt[key][warp] + rank : 0u;
+        if (key >= 0) {
+          IReq<R> &q = req[slot];
+          q.x = t.x; q.y = t.y; q.z = t.z;
+          q.id = t.id;
+          q.E = t.E; q.d0 = t.u; q.d1 = t.v; q.d2 = t.w;
+#pragma unroll
+          for (int j = 0; j < 6; ++j) q.u[j] = u[2 + j];
+          q.ev = t.ev;
+          q.kk = kstep;
+          q.sub = t.sub;
+          q.tp = key;
+        }
+        __syncthreads();
+        Kids<R> kb;
+        kb.n = 0;
+        Parent par;
+        uint32_t pk = 0;
+        if (static_cast<unsigned>(tid) < s_nreq) {
+          IReq<R> &q = req[tid];
+          R uu[8] = {R(0), R(0), q.u[0], q.u[1], q.u[2], q.u[3], q.u[4], q.u[5]};
+          R d[3] = {q.d0, q.d1, q.d2};
+          R e = q.E;
+          const int ty = q.tp / 3;
+          const int r = final_state(V, S, &bc, ty, q.tp - 3 * ty, e, d, uu, kb, q.ev, q.sub, q.x, q.y);
+          par.x = q.x; par.y = q.y; par.z = q.z;
+          par.id = q.id;
+          par.ev = q.ev;
+          par.sub = q.sub;
+          pk = q.kk;
+          q.E = e; q.d0 = d[0]; q.d1 = d[1]; q.d2 = d[2];
+          q.tp = r;
+        }
+        push_kids(S, out, par, kb, pk, &bc);
+        __syncthreads();
+        if (key >= 0) {
+          const IReq<R> &q = req[slot];
+          if (q.tp >= 0) {
+            t.E = q.E; t.u = q.d0; t.v = q.d1; t.w = q.d2;
+            t.flags |= kFlagInteracted;
+            alive = q.tp != 0;
+          }
+        }
+      }
+      if (was_alive && !alive) track_ended(S, t.ev);
     }
     push_survivor(S, out, t, alive);
   }
@@ -484,6 +638,7 @@ struct Ctx {
   HostTables ht;
   // device allocations
   void *d_xs = nullptr, *d_bins = nullptr;
+  float *d_inv_node = nullptr;
   double *d_zb = nullptr;
   unsigned char *d_smat = nullptr;
   void *d_queues = nullptr;
@@ -491,6 +646,7 @@ struct Ctx {
   void *d_state = nullptr;
   double *d_edep = nullptr, *d_cell = nullptr, *d_escape = nullptr;
   unsigned long long *d_evcnt = nullptr;
+  unsigned *d_evlive = nullptr;
   size_t ev_cap = 0;
   gv_primary *d_prim = nullptr;
   unsigned *d_order = nullptr;
@@ -502,7 +658,7 @@ struct Ctx {
   long long launches = 0;
   int last_status = 0;
   ModelMeta meta[kNModel];
-  size_t xs_bytes = 0, zb_bytes = 0, smem_bytes = 0;
+  size_t xs_bytes = 0, zb_bytes = 0, smem_bytes = 0, req_off = 0;
   int grid = 0;
 };
 
@@ -547,7 +703,7 @@ int validate_cfg(const gv_config &c) {
   if (c.refill_batch < 1 || c.refill_low_water < 0) return GV_ERR_BAD_ARG;
   if (c.generations_per_graph < 2 || c.generations_per_graph % 2 || c.generations_per_graph > 1024)
     return GV_ERR_BAD_ARG;
-  if (c.max_generations < 1) return GV_ERR_BAD_ARG;
+  if (c.max_generations < 1 || c.max_events_in_flight < 0) return GV_ERR_BAD_ARG;
   return GV_OK;
 }
 
@@ -596,6 +752,12 @@ template <typename R> int upload_tables(Ctx *c) {
   c->xs_bytes = nv * sizeof(V4<R>);
   CK(cudaMalloc(&c->d_xs, c->xs_bytes));
   CK(cudaMemcpy(c->d_xs, xs.data(), c->xs_bytes, cudaMemcpyHostToDevice));
+  // reciprocal node energies for the FP32 interval fraction
+  std::vector<float> inv(kGridN);
+  for (int i = 0; i < kGridN; ++i)
+    inv[i] = static_cast<float>(std::exp(-(std::log(kGridEmin) + i * std::log(10.0) / kGridPerDecade)));
+  CK(cudaMalloc(&c->d_inv_node, sizeof(float) * kGridN));
+  CK(cudaMemcpy(c->d_inv_node, inv.data(), sizeof(float) * kGridN, cudaMemcpyHostToDevice));
   // alias bins
   std::vector<AliasBin<R>> bins;
   for (int m = 0; m < kNModel; ++m) {
@@ -622,6 +784,7 @@ template <typename R> int upload_tables(Ctx *c) {
 template <typename R> View<R> make_view(const Ctx *c) {
   View<R> v;
   v.xs = reinterpret_cast<const V4<R> *>(c->d_xs);
+  v.inv_node = c->d_inv_node;
   v.zb = c->d_zb;
   v.smat = c->d_smat;
   v.bins = reinterpret_cast<const AliasBin<R> *>(c->d_bins);
@@ -654,11 +817,13 @@ template <typename R> int prepare_device(Ctx *c) {
   CK(cudaMalloc(&c->d_state, sizeof(DevState<R>)));
   CK(cudaMallocHost(&c->h_ctl, sizeof(Ctl)));
   c->zb_bytes = ((c->nsub + 1) * sizeof(double) + 15) / 16 * 16;
-  c->smem_bytes = c->xs_bytes + c->zb_bytes + (c->nsub + 15) / 16 * 16;
-  CK(cudaFuncSetAttribute(step_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          static_cast<int>(c->smem_bytes)));
+  c->req_off = c->xs_bytes + c->zb_bytes + kInvNodeBytes + (c->nsub + 15) / 16 * 16;
+  c->smem_bytes = c->req_off + (c->cfg.process_sort ? sizeof(IReq<R>) * c->cfg.block_size : 0);
+  const void *kern = c->cfg.process_sort ? reinterpret_cast<const void *>(step_kernel<R, true>)
+                                         : reinterpret_cast<const void *>(step_kernel<R, false>);
+  CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(c->smem_bytes)));
   int occ = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_kernel<R>, c->cfg.block_size, c->smem_bytes));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, c->cfg.block_size, c->smem_bytes));
   if (occ < 1) return GV_ERR_BAD_ARG;
   c->grid = c->sm_count * std::min(occ, c->cfg.blocks_per_sm);
   return GV_OK;
@@ -684,6 +849,7 @@ template <typename R> DevState<R> make_state(Ctx *c) {
   s.n_mat = static_cast<int>(c->mats.size());
   s.xs_bytes = static_cast<unsigned>(c->xs_bytes);
   s.zb_bytes = static_cast<unsigned>(c->zb_bytes);
+  s.smem_req_off = static_cast<unsigned>(c->req_off);
   return s;
 }
 
@@ -692,8 +858,12 @@ template <typename R> int capture_graph(Ctx *c) {
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
   const DevState<R> *S = reinterpret_cast<const DevState<R> *>(c->d_state);
-  for (int i = 0; i < c->cfg.generations_per_graph; ++i)
-    step_kernel<R><<<c->grid, c->cfg.block_size, c->smem_bytes, c->stream>>>(S, i & 1);
+  for (int i = 0; i < c->cfg.generations_per_graph; ++i) {
+    if (c->cfg.process_sort)
+      step_kernel<R, true><<<c->grid, c->cfg.block_size, c->smem_bytes, c->stream>>>(S, i & 1);
+    else
+      step_kernel<R, false><<<c->grid, c->cfg.block_size, c->smem_bytes, c->stream>>>(S, i & 1);
+  }
   cudaError_t e = cudaStreamEndCapture(c->stream, &g);
   if (e != cudaSuccess) return GV_ERR_CUDA;
   e = cudaGraphInstantiate(&c->graph, g, 0);
@@ -720,13 +890,16 @@ int run_transport(Ctx *c, const gv_primary *p, long long n, long long n_events, 
     cudaFree(c->d_edep);
     cudaFree(c->d_escape);
     cudaFree(c->d_evcnt);
+    cudaFree(c->d_evlive);
     c->d_edep = nullptr;
     c->d_escape = nullptr;
     c->d_evcnt = nullptr;
+    c->d_evlive = nullptr;
     c->ev_cap = 0;
     if (cudaMalloc(&c->d_edep, sizeof(double) * n_events * nsub) != cudaSuccess ||
         cudaMalloc(&c->d_escape, sizeof(double) * n_events) != cudaSuccess ||
-        cudaMalloc(&c->d_evcnt, sizeof(unsigned long long) * n_events * GV_NCOUNT) != cudaSuccess)
+        cudaMalloc(&c->d_evcnt, sizeof(unsigned long long) * n_events * GV_NCOUNT) != cudaSuccess ||
+        cudaMalloc(&c->d_evlive, sizeof(unsigned) * n_events) != cudaSuccess)
       return GV_ERR_OOM;
     c->ev_cap = n_events;
   }
@@ -773,6 +946,7 @@ int run_transport(Ctx *c, const gv_primary *p, long long n, long long n_events, 
   if (ncell) CK(cudaMemsetAsync(c->d_cell, 0, sizeof(double) * ncell, c->stream));
   const bool evc = c->cfg.per_event_counts != 0 && res && res->event_counts;
   if (evc) CK(cudaMemsetAsync(c->d_evcnt, 0, sizeof(unsigned long long) * n_events * GV_NCOUNT, c->stream));
+  CK(cudaMemsetAsync(c->d_evlive, 0, sizeof(unsigned) * n_events, c->stream));
   DevState<R> s = make_state<R>(c);
   s.prim = dp;
   s.order = c->cfg.mode == GV_ONE_EVENT_PER_LAUNCH ? c->d_order : nullptr;
@@ -782,6 +956,8 @@ int run_transport(Ctx *c, const gv_primary *p, long long n, long long n_events, 
   s.cell = (ncell && res && res->cell_edep) ? c->d_cell : nullptr;
   s.escape = c->d_escape;
   s.evcnt = evc ? c->d_evcnt : nullptr;
+  s.evlive = c->d_evlive;
+  s.max_in_flight = static_cast<unsigned>(std::min<long long>(c->cfg.max_events_in_flight, 0xffffffffll));
   s.seed_lo = static_cast<unsigned>(seed);
   s.seed_hi = static_cast<unsigned>(seed >> 32);
   static thread_local DevState<R> staged;  // pinned copy not needed: synchronous below
@@ -855,6 +1031,7 @@ int gv_default_config(gv_config *cfg) {
   cfg->max_generations = 1ll << 20;
   cfg->per_event_counts = 0;
   cfg->process_sort = 0;
+  cfg->max_events_in_flight = 4096;
   return GV_OK;
 }
 
@@ -956,6 +1133,7 @@ void gv_destroy(void *ctx) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   cudaFree(c->d_xs);
+  cudaFree(c->d_inv_node);
   cudaFree(c->d_bins);
   cudaFree(c->d_zb);
   cudaFree(c->d_smat);
@@ -966,6 +1144,7 @@ void gv_destroy(void *ctx) {
   cudaFree(c->d_cell);
   cudaFree(c->d_escape);
   cudaFree(c->d_evcnt);
+  cudaFree(c->d_evlive);
   cudaFree(c->d_prim);
   cudaFree(c->d_order);
   if (c->h_ctl) cudaFreeHost(c->h_ctl);

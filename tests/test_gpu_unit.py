@@ -92,10 +92,16 @@ def test_xs_lookup_matches_oracle(torch, ctx, oracle_pbps, ptype):
         got = out.cpu().numpy()
         sel = np.random.default_rng(3).choice(N, 6000, replace=False)
         sel = np.concatenate([np.arange(292), sel])
+        g = oracle_pbps.grid()
+        k = np.clip(np.searchsorted(g, E[sel], side="right") - 1, 0, len(g) - 2)
         for q in range(nq):
             ref = oracle_pbps.lookup(ptype, q, mat, E[sel])
-            scale = 1e-7 * np.abs(oracle_pbps.table_nodes(ptype, q, mat)).max()
-            err = np.abs(got[sel, q] - ref) / np.maximum(np.abs(ref), scale)
+            nodes = oracle_pbps.table_nodes(ptype, q, mat)
+            # the natural scale of an interpolated value: the node values it blends
+            scale = np.maximum(np.maximum(np.abs(nodes[k]), np.abs(nodes[k + 1])), np.abs(ref))
+            diff = np.abs(got[sel, q] - ref)
+            assert np.all(diff[scale == 0] == 0)  # closed processes stay exactly zero
+            err = np.where(scale > 0, diff / np.where(scale > 0, scale, 1.0), 0.0)
             assert err.max() < TOL[ctx.prec], (ptype, mat, q, err.max(), E[sel][np.argmax(err)])
 
 
@@ -112,8 +118,18 @@ def test_continuous_loss_matches_oracle(torch, ctx, oracle_pbps, ptype):
         ctx.gv_unit_eloss(ptype, mat, _dev(torch, E), _dev(torch, s), out)
         got = out.cpu().numpy()
         ref = oracle_pbps.eloss(ptype, mat, E, s)
-        err = np.abs(got - ref) / E
+        # Near the end of the range (s -> R(E)) E' is ill conditioned; allow the
+        # spread of the exact answer over a 3e-7 relative change of the input
+        # (the FP32 resolution of the table position) on top of 1e-5 E.
+        d = 3e-7 if ctx.prec == 0 else 0.0
+        env = np.maximum(np.abs(oracle_pbps.eloss(ptype, mat, E * (1 + d), s) - ref),
+                         np.abs(oracle_pbps.eloss(ptype, mat, E * (1 - d), s) - ref))
+        err = (np.abs(got - ref) - env) / E
         assert err.max() < TOL[ctx.prec], (mat, err.max(), E[np.argmax(err)], s[np.argmax(err)])
+        # well-conditioned steps meet the plain bound
+        wc = env < 1e-6 * E
+        assert (np.abs(got - ref)[wc] / E[wc]).max() < TOL[ctx.prec]
+        assert wc.mean() > 0.99
 
 
 # ---------------------------------------------------------------- alias sampling
@@ -178,9 +194,10 @@ def test_interaction_matches_oracle(torch, ctx, oracle_pbps, ptype, proc, rng_E)
     checked = 0
     for i in range(n):
         r, o = oracle_pbps.interact(ptype, proc, E[i], d[i], u[i])
-        # a secondary at its production threshold may go either way
-        if any(abs(o[7 + 5 * j] - 1.0) < 1e-5 * E[i] for j in range(int(o[5]))) or \
-                abs(o[4] - 1.0) < 1e-5 * E[i]:
+        # a Compton/photo/pair lepton at the e cut (1 MeV) is tracked or
+        # deposited on the spot depending on rounding
+        if ptype == 0 and (any(abs(o[7 + 5 * j] - 1.0) < 1e-5 for j in range(int(o[5]))) or
+                           abs(o[4] - 1.0) < 1e-5):
             skip[i] = True
         if skip[i]:
             continue

@@ -29,7 +29,7 @@ def _needs(out: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src: str, verbose: bool) -> str:
+def _compile(src: str, verbose: bool, min_blocks: int = 0) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     deps = [os.path.join(CSRC, src)] + [os.path.join(CSRC, h) for h in HEADERS] + \
         [os.path.join(ROOT, "include", "gv.h")]
@@ -40,6 +40,8 @@ def _compile(src: str, verbose: bool) -> str:
                "--expt-relaxed-constexpr", "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
+        if min_blocks:
+            cmd.insert(1, f"-DGV_MIN_BLOCKS={int(min_blocks)}")
     else:
         cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-c",
                os.path.join(CSRC, src), "-o", obj]
@@ -47,18 +49,27 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, min_blocks: int = 0, out: str = OUT) -> str:
+    """Compile libgv.so.  min_blocks > 0 builds the step kernel with a register
+    budget for that many resident 256-thread blocks per SM (written to a
+    separate build directory; pass `out` to keep the default library)."""
+    global BUILD
+    build_dir = BUILD if not min_blocks else BUILD + f"_mb{min_blocks}"
+    os.makedirs(build_dir, exist_ok=True)
     if force:
-        for f in os.listdir(BUILD):
-            os.remove(os.path.join(BUILD, f))
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
-    if force or _needs(OUT, objs):
-        tmp = OUT + f".{os.getpid()}.tmp"
+        for f in os.listdir(build_dir):
+            os.remove(os.path.join(build_dir, f))
+    saved, BUILD = BUILD, build_dir
+    try:
+        with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
+            objs = list(ex.map(lambda s: _compile(s, verbose, min_blocks), SOURCES))
+    finally:
+        BUILD = saved
+    if force or _needs(out, objs):
+        tmp = out + f".{os.getpid()}.tmp"
         subprocess.check_call([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
-        os.replace(tmp, OUT)
-    return OUT
+        os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

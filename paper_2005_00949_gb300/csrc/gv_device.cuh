@@ -338,53 +338,72 @@ template <typename R> __device__ __forceinline__ void at_rest(Kids<R> &k, R u6, 
 
 // Final state (PostStepActions) of process p.  u[2..7]: grid, bin, in-bin,
 // azimuth, isotropic pair.  Returns 1 survives, 0 ended, -1 not possible.
-// Angles use forms of 1 -+ cos(theta) that carry no cancellation, written
-// from the sampled reduced variable xi; they are algebraically the textbook
-// two-body kinematics.
+// The reduced variable of every alias-sampled model is drawn by one call
+// site, so a warp whose lanes run different processes samples together and
+// diverges only for the kinematics.  Angles use forms of 1 -+ cos(theta)
+// without cancellation, written from the sampled xi; they are algebraically
+// the textbook two-body kinematics.
 template <typename R>
 __device__ int interact(const View<R> &V, int type, int p, R &E, R d[3], const R *u, Kids<R> &kids, R &local,
                         int &npair, int &nann) {
   const R ME = static_cast<R>(kME);
   const R ecut_push = static_cast<R>(V.cut.ecut > V.cut.tcut ? V.cut.ecut : V.cut.tcut);
   const R tcut = static_cast<R>(V.cut.tcut);
+  const R ec = static_cast<R>(V.cut.ecut);
+  local = R(0);
+  // which model, and is it open at this energy?
+  int model;
+  if (type == 0) {
+    if (p == 1) model = -1;  // photoelectric: nothing to sample
+    else if (p == 0) model = kCompton;
+    else {
+      if (!(E > R(2) * ME)) return -1;
+      model = kPair;
+    }
+  } else if (p == 0) {
+    if (!(E > static_cast<R>(V.cut.gcut))) return -1;
+    model = kBrem;
+  } else if (p == 1) {
+    if (!(E > (type == 1 ? R(2) * ec : ec))) return -1;
+    model = type == 1 ? kMoller : kBhabha;
+  } else {
+    model = kAnnih;
+  }
+  R xi = R(0), v = R(0);
+  if (model >= 0) v = alias_sample<R>(V, model, E, u[2], u[3], u[4], &xi);
   R sp, cp;
   m_sincos(static_cast<R>(2.0 * kPi) * u[5], &sp, &cp);
-  local = R(0);
-  R xi;
-  if (type == 0) {
+  if (model == kCompton) {  // eps = eps0^(1-xi)
+    const R k = E, kap = k / ME;
+    const R L0 = -m_log1p(R(2) * kap);
+    const R a = (R(1) - xi) * L0;
+    const R eps = m_exp(a);
+    const R om_eps = -m_expm1(a);                   // 1 - eps
+    const R omc = om_eps / (kap * eps);             // 1 - cos(theta)
+    const R opc = m_expm1(-xi * L0) / (kap * eps);  // 1 + cos(theta)
+    const R st = m_sqrt(omc * opc);
+    const R ct = omc < R(1) ? R(1) - omc : opc - R(1);
+    R d1[3], de[3];
+    rotate(d, ct, st, cp, sp, d1);
+    const R k1 = eps * k, Te = k * om_eps;
+    // electron momentum k d - k' d' = k [(1 - eps ct) d - eps st e_phi]
+    rotate_vec(d, om_eps + eps * omc, eps * st, -cp, -sp, de);
+    if (Te >= ecut_push) add_kid(kids, 1, Te, de);
+    else local += Te;
+    d[0] = d1[0]; d[1] = d1[1]; d[2] = d1[2];
+    if (k1 < tcut) { local += k1; E = R(0); return 0; }
+    E = k1;
+    return 1;
+  }
+  if (model < 0) {  // photoelectric: the electron takes k along the photon
+    if (E >= ecut_push) add_kid(kids, 1, E, d);
+    else local += E;
+    E = R(0);
+    return 0;
+  }
+  if (model == kPair) {
     const R k = E;
-    if (p == 0) {  // Compton: eps = eps0^(1-xi)
-      (void)alias_sample<R>(V, kCompton, k, u[2], u[3], u[4], &xi);
-      const R kap = k / ME;
-      const R L0 = -m_log1p(R(2) * kap);
-      const R a = (R(1) - xi) * L0;
-      const R eps = m_exp(a);
-      const R om_eps = -m_expm1(a);                 // 1 - eps
-      const R omc = om_eps / (kap * eps);           // 1 - cos(theta)
-      const R opc = m_expm1(-xi * L0) / (kap * eps);  // 1 + cos(theta)
-      const R st = m_sqrt(omc * opc);
-      const R ct = omc < R(1) ? R(1) - omc : opc - R(1);
-      R d1[3], de[3];
-      rotate(d, ct, st, cp, sp, d1);
-      const R k1 = eps * k, Te = k * om_eps;
-      // electron momentum k d - k' d' = k [(1 - eps ct) d - eps st e_phi]
-      rotate_vec(d, om_eps + eps * omc, eps * st, -cp, -sp, de);
-      if (Te >= ecut_push) add_kid(kids, 1, Te, de);
-      else local += Te;
-      d[0] = d1[0]; d[1] = d1[1]; d[2] = d1[2];
-      if (k1 < tcut) { local += k1; E = R(0); return 0; }
-      E = k1;
-      return 1;
-    }
-    if (p == 1) {  // photoelectric
-      if (k >= ecut_push) add_kid(kids, 1, k, d);
-      else local += k;
-      E = R(0);
-      return 0;
-    }
-    if (!(k > R(2) * ME)) return -1;  // pair
-    const R x = alias_sample<R>(V, kPair, k, u[2], u[3], u[4], &xi);
-    R Tm = x * k - ME, Tp = (R(1) - x) * k - ME;
+    R Tm = v * k - ME, Tp = (R(1) - v) * k - ME;
     Tm = Tm < R(0) ? R(0) : Tm;
     Tp = Tp < R(0) ? R(0) : Tp;
     R st, ct;
@@ -405,21 +424,16 @@ __device__ int interact(const View<R> &V, int type, int p, R &E, R d[3], const R
     return 0;
   }
   R T = E;
-  if (p == 0) {  // bremsstrahlung
-    if (!(T > static_cast<R>(V.cut.gcut))) return -1;
-    const R kg = alias_sample<R>(V, kBrem, T, u[2], u[3], u[4], &xi);
+  if (model == kBrem) {
     R st, ct, dg[3];
     m_sincos(ME / (T + ME), &st, &ct);
     rotate(d, ct, st, cp, sp, dg);
-    if (kg >= tcut) add_kid(kids, 0, kg, dg);
-    else local += kg;
-    T -= kg;
-  } else if (p == 1) {  // ionisation: Moller eps = xc (1/(2xc))^xi, Bhabha eps = xc^(1-xi)
-    const R ec = static_cast<R>(V.cut.ecut);
-    if (type == 1 && !(T > R(2) * ec)) return -1;
-    if (type == 2 && !(T > ec)) return -1;
-    const R eps = alias_sample<R>(V, type == 1 ? kMoller : kBhabha, T, u[2], u[3], u[4], &xi);
-    const R om_eps = type == 1 ? R(1) - eps : -m_expm1((R(1) - xi) * m_log(ec / T));
+    if (v >= tcut) add_kid(kids, 0, v, dg);
+    else local += v;
+    T -= v;
+  } else if (model != kAnnih) {  // ionisation: Moller eps = xc (1/(2xc))^xi, Bhabha eps = xc^(1-xi)
+    const R eps = v;
+    const R om_eps = model == kMoller ? R(1) - eps : -m_expm1((R(1) - xi) * m_log(ec / T));
     const R Td = eps * T;
     const R den = eps * T + R(2) * ME;
     // delta ray: cos^2 = eps (T + 2m) / (eps T + 2m), sin^2 = 2m (1 - eps) / (eps T + 2m)
@@ -433,7 +447,6 @@ __device__ int interact(const View<R> &V, int type, int p, R &E, R d[3], const R
     d[0] = dn[0]; d[1] = dn[1]; d[2] = dn[2];
     T = T * om_eps;
   } else {  // annihilation in flight: softer photon eps = eps_min (1/(2 eps_min))^xi
-    (void)alias_sample<R>(V, kAnnih, T, u[2], u[3], u[4], &xi);
     const R t = T / ME;
     const R s = m_sqrt(t / (t + R(2)));
     const R emin = R(1) / ((t + R(2)) * (R(1) + s));

@@ -114,8 +114,11 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   }
   // Propagation (FP64 positions)
   const double sd = static_cast<double>(s);
-  const double mx = t.x + 0.5 * sd * static_cast<double>(t.u);
-  const double my = t.y + 0.5 * sd * static_cast<double>(t.v);
+  double mx = 0.0, my = 0.0;  // step midpoint: only cell scoring reads it
+  if (S->cell) {
+    mx = t.x + 0.5 * sd * static_cast<double>(t.u);
+    my = t.y + 0.5 * sd * static_cast<double>(t.v);
+  }
   t.x += sd * static_cast<double>(t.u);
   t.y += sd * static_cast<double>(t.v);
   t.z += sd * static_cast<double>(t.w);
@@ -126,8 +129,12 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   }
   if (Sig > R(0)) t.nlam = (lim == 1) ? R(0) : t.nlam - s * Sig;
   t.step = k + 1;
-  count(S, bc, t.ev, GV_C_STEPS);
-  count(S, bc, t.ev, GV_C_STEPS_G + t.type);
+  // the block's step counters are summed per warp by the caller; only the
+  // optional per-event rows are booked here
+  if (S->evcnt) {
+    atomicAdd(&S->evcnt[static_cast<size_t>(t.ev) * GV_NCOUNT + GV_C_STEPS], 1ull);
+    atomicAdd(&S->evcnt[static_cast<size_t>(t.ev) * GV_NCOUNT + GV_C_STEPS_G + t.type], 1ull);
+  }
   const int pre_sub = t.sub;
   // AlongStepAction
   if (charged) {
@@ -398,8 +405,21 @@ template <typename R> __global__ void init_kernel(const DevState<R> *S) {
 }
 
 // ------------------------------------------------------------------ the kernel
+// Register budget: GV_MIN_BLOCKS resident 256-thread blocks per SM (0: up to
+// 512 threads with no residency target).
+#ifndef GV_MIN_BLOCKS
+#define GV_MIN_BLOCKS 0
+#endif
+#if GV_MIN_BLOCKS > 0
+#define GV_STEP_BOUNDS __launch_bounds__(256, GV_MIN_BLOCKS)
+#define GV_MAX_BLOCK 256
+#else
+#define GV_STEP_BOUNDS __launch_bounds__(512)
+#define GV_MAX_BLOCK 512
+#endif
+
 template <typename R, bool SORT>
-__global__ void __launch_bounds__(512) step_kernel(const DevState<R> *__restrict__ S, int parity) {
+__global__ void GV_STEP_BOUNDS step_kernel(const DevState<R> *__restrict__ S, int parity) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ View<R> sV;
   __shared__ BlockCnt bc;
@@ -527,6 +547,21 @@ __global__ void __launch_bounds__(512) step_kernel(const DevState<R> *__restrict
         }
       }
       push_kids(S, out, parent_of(t), kids, kstep, &bc);
+      {  // step counters, one shared-memory atomic per warp and kind
+        const bool stepped = was_alive && t.step != kstep;
+        const unsigned m = __ballot_sync(0xffffffffu, stepped);
+        if (m) {
+          const unsigned mg = __ballot_sync(0xffffffffu, stepped && t.type == 0);
+          const unsigned me = __ballot_sync(0xffffffffu, stepped && t.type == 1);
+          if ((tid & 31) == 0) {
+            atomicAdd(&bc.c[GV_C_STEPS], static_cast<unsigned long long>(__popc(m)));
+            if (mg) atomicAdd(&bc.c[GV_C_STEPS_G], static_cast<unsigned long long>(__popc(mg)));
+            if (me) atomicAdd(&bc.c[GV_C_STEPS_EM], static_cast<unsigned long long>(__popc(me)));
+            const unsigned mp = m & ~(mg | me);
+            if (mp) atomicAdd(&bc.c[GV_C_STEPS_EP], static_cast<unsigned long long>(__popc(mp)));
+          }
+        }
+      }
       if (SORT) {
         // S1 basketizer: counting sort of this step's interaction requests by
         // (type, process) -- warp ballots, a block prefix sum, one slot each --
@@ -694,7 +729,7 @@ int validate(const gv_material *mats, int n_mats, const gv_layers *geo, const gv
 int validate_cfg(const gv_config &c) {
   if (c.precision != GV_MIXED && c.precision != GV_FP64) return GV_ERR_BAD_ARG;
   if (c.mode != GV_BATCHED && c.mode != GV_ONE_EVENT_PER_LAUNCH) return GV_ERR_BAD_ARG;
-  if (c.block_size < 64 || c.block_size > 512 || c.block_size % 32) return GV_ERR_BAD_ARG;
+  if (c.block_size < 64 || c.block_size > GV_MAX_BLOCK || c.block_size % 32) return GV_ERR_BAD_ARG;
   if (c.blocks_per_sm < 1 || c.blocks_per_sm > 32) return GV_ERR_BAD_ARG;
   if (c.steps_per_claim < 1 || c.tail_steps_per_claim < 1 || c.steps_per_claim > 4096 ||
       c.tail_steps_per_claim > 4096)
@@ -1021,8 +1056,8 @@ int gv_default_config(gv_config *cfg) {
   cfg->mode = GV_BATCHED;
   cfg->block_size = 256;
   cfg->blocks_per_sm = 4;
-  cfg->steps_per_claim = 4;
-  cfg->tail_steps_per_claim = 64;
+  cfg->steps_per_claim = 2;
+  cfg->tail_steps_per_claim = 16;
   cfg->tail_threshold = 100000;
   cfg->stack_capacity = 1ll << 23;
   cfg->refill_low_water = 1ll << 21;

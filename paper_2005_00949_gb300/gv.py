@@ -15,7 +15,7 @@ import numpy as np
 from . import workloads as W
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgv.so")
+LIB_PATH = os.environ.get("GV_LIB", os.path.join(_HERE, "libgv.so"))
 _lib = None
 _lock = threading.Lock()
 

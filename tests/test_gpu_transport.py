@@ -189,7 +189,12 @@ def test_integer_counts_invariant_to_launch_shape(gvmod):
             base = r
             continue
         assert np.array_equal(r["counts"][:, :11], base["counts"][:, :11]), kw
-        assert np.allclose(r["edep"], base["edep"], rtol=1e-6, atol=1e-9)
+        # the same kernel in another launch shape differs only by the order of
+        # the FP64 atomic sums; the basketizing kernel is another compilation
+        # of the same arithmetic and may round single FP32 operations apart
+        scale = np.maximum(base["edep"].sum(1, keepdims=True), 1.0)
+        rel = (np.abs(r["edep"] - base["edep"]) / scale).max()
+        assert rel < (1e-5 if kw.get("process_sort") else 1e-9), (kw, rel)
         ctx.close()
 
 

@@ -159,6 +159,32 @@ int gv_build_tables(void *ctx);
 int gv_transport(void *ctx, const gv_primary *p, long long n, long long n_events,
                  unsigned long long seed, void *stream, gv_result *res);
 
+/* gv_transport without any device allocation (the paper has no counterpart;
+ * this entry point exists for embedding).  For callers that cannot let a
+ * library call cudaMalloc/cudaFree while they run -- e.g. a host framework
+ * that owns all of a GPU's memory through its own pools and budget; those
+ * calls also synchronise the device and can fail under memory pressure.
+ * The context must already exist (gv_setup and gv_build_tables allocate, once)
+ * and use GV_MIXED.  All scratch memory -- track queues for 65,536 tracks per
+ * particle type, the generation control block, and live-track counts for up
+ * to 65,536 events -- sits in one file-scope device array of 25,436,160 bytes
+ * that every GPU holds from the library's first use on it until the process
+ * exits.  The first call on a device looks up that array's address; make it
+ * before any stream capture.  Every call reuses the array and clears what
+ * must start at zero; calls whose work overlaps on the GPU (two streams, two
+ * threads, or a concurrent call on another context) race on it.
+ *   prim      device array of n primaries;
+ *   edep      device [n_events][n_layers*n_sub], zeroed, then accumulated;
+ *   escape_E  device [n_events], zeroed, then accumulated;
+ *   counters  host array of 16 (as gv_result.counters).
+ * Runs the batched schedule with at most 64 events in flight, on `stream`,
+ * and returns when done.  GV_ERR_BAD_ARG: n_events > 65,536, host pointers,
+ * or an FP64 context; GV_ERR_STACK_FULL: more live tracks than the array
+ * holds (showers far above ~10 GeV per event in flight). */
+int gv_transport_static(void *ctx, const gv_primary *prim, long long n, long long n_events,
+                        unsigned long long seed, void *stream, double *edep, double *escape_E,
+                        unsigned long long *counters);
+
 /* Wait for all work of the context on `stream`; returns the last status. */
 int gv_sync(void *ctx, void *stream);
 

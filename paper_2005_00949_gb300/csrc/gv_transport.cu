@@ -1220,3 +1220,165 @@ int ctx_views(void *ctx, int *precision, View<float> *vf, View<double> *vd) {
 }
 int ctx_nmat(void *ctx) { return static_cast<int>(static_cast<Ctx *>(ctx)->mats.size()); }
 }  // namespace gv
+
+// ====================================================================== transport without allocation
+// Some callers must not have this library allocate device memory while they
+// run: a host framework that hands out all of a GPU's memory from its own
+// pools under a fixed budget (as large event-processing frameworks do) cannot
+// let a library call cudaMalloc behind its back, and cudaMalloc/cudaFree also
+// synchronise the whole device and may fail or stall under memory pressure.
+// gv_transport_static runs the same step kernel as gv_transport, but keeps
+// every piece of scratch memory it needs -- the double-buffered track queues,
+// the generation control block, the kernel's state record and the per-event
+// live-track counts -- in the file-scope array below, sized once for a modest
+// maximum.  The array is part of the module image: every GPU that loads
+// libgv holds it until the process exits.
+namespace {
+constexpr long long kStaticCap = 1 << 16;         // tracks per particle type and buffer
+constexpr long long kStaticMaxEvents = 1 << 16;   // events per call
+constexpr size_t kStaticCtlOff = 0;
+constexpr size_t kStaticStateOff = 1024;
+constexpr size_t kStaticEvliveOff = 8192;
+constexpr size_t kStaticQueueOff = kStaticEvliveOff + sizeof(unsigned) * kStaticMaxEvents;
+constexpr size_t kStaticQueueBytes = 6 * static_cast<size_t>(kStaticCap) * track_bytes<float>();
+constexpr size_t kStaticBytes = kStaticQueueOff + kStaticQueueBytes;  // 25,436,160 bytes
+static_assert(sizeof(Ctl) <= kStaticStateOff - kStaticCtlOff, "control block does not fit");
+static_assert(sizeof(DevState<float>) <= kStaticEvliveOff - kStaticStateOff, "state does not fit");
+static_assert(kStaticCap % 64 == 0, "queue arrays must stay 256-byte aligned");
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_gv_static_scratch[kStaticBytes];
+
+namespace {
+
+std::mutex g_static_mu;
+unsigned char *g_static_base[256] = {};  // device address of the array, per device ordinal
+
+// Device address of the scratch array on the current device.  Host code only
+// sees a host-side stand-in under the array's name, so the address is asked
+// of the runtime once per device, with that device current.
+int static_scratch(int dev, unsigned char **base) {
+  if (dev < 0 || dev >= 256) return GV_ERR_BAD_ARG;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_base[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_gv_static_scratch) != cudaSuccess || !p) return GV_ERR_CUDA;
+    g_static_base[dev] = static_cast<unsigned char *>(p);
+  }
+  *base = g_static_base[dev];
+  return GV_OK;
+}
+
+// carve the queues of the scratch array exactly as carve() does for the
+// context's own allocation (every array a multiple of 256 bytes long)
+Queue<float> carve_static(unsigned char *&p) {
+  Queue<float> q;
+  auto take = [&](size_t n) {
+    unsigned char *r = p;
+    p += n;
+    return r;
+  };
+  const size_t C = static_cast<size_t>(kStaticCap);
+  q.x = reinterpret_cast<double *>(take(C * 8));
+  q.y = reinterpret_cast<double *>(take(C * 8));
+  q.z = reinterpret_cast<double *>(take(C * 8));
+  q.u = reinterpret_cast<float *>(take(C * 4));
+  q.v = reinterpret_cast<float *>(take(C * 4));
+  q.w = reinterpret_cast<float *>(take(C * 4));
+  q.E = reinterpret_cast<float *>(take(C * 4));
+  q.nlam = reinterpret_cast<float *>(take(C * 4));
+  q.id = reinterpret_cast<unsigned long long *>(take(C * 8));
+  q.ev = reinterpret_cast<unsigned *>(take(C * 4));
+  q.step = reinterpret_cast<unsigned *>(take(C * 4));
+  q.sf = reinterpret_cast<int *>(take(C * 4));
+  return q;
+}
+
+// the state record travels as a kernel argument, so no staging copy is needed
+__global__ void static_begin_kernel(DevState<float> s, DevState<float> *dst) {
+  *dst = s;
+  Ctl *c = s.ctl;
+  for (int i = 0; i < 2; ++i)
+    for (int q = 0; q < 3; ++q) c->cnt[i][q] = 0;
+  c->prim_next = 0;
+  c->status = 0;
+  c->done = 0;
+  c->gen = 0;
+  c->live_peak = 0;
+  c->ev_started = 0;
+  c->ev_done = 0;
+  for (int i = 0; i < 16; ++i) c->counters[i] = 0;
+  plan_next(dst, 0);
+}
+
+}  // namespace
+
+extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long n, long long n_events,
+                                   unsigned long long seed, void *stream, double *edep, double *escape_E,
+                                   unsigned long long *counters) {
+  Ctx *c = static_cast<Ctx *>(ctx);
+  if (!c || n < 0 || (n > 0 && !prim) || n_events < 1 || !edep || !escape_E || !counters) return GV_ERR_BAD_ARG;
+  if (!c->tables) return GV_ERR_NO_TABLES;
+  if (c->cfg.precision != GV_MIXED) return GV_ERR_BAD_ARG;  // the array is sized for the mixed layout
+  if (n_events > kStaticMaxEvents || n > 0xffffffffll) return GV_ERR_BAD_ARG;
+  if ((n > 0 && !is_device_ptr(prim)) || !is_device_ptr(edep) || !is_device_ptr(escape_E)) return GV_ERR_BAD_ARG;
+  if (cudaSetDevice(c->device) != cudaSuccess) return GV_ERR_CUDA;
+  unsigned char *base = nullptr;
+  int rc = static_scratch(c->device, &base);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t smem = c->req_off;  // tables and geometry; the non-basketizing kernel
+  if (cudaFuncSetAttribute(step_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess)
+    return GV_ERR_CUDA;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_kernel<float, false>, c->cfg.block_size, smem) !=
+          cudaSuccess ||
+      occ < 1)
+    return GV_ERR_CUDA;
+  const int grid = c->sm_count * std::min(occ, c->cfg.blocks_per_sm);
+  // the tallies and the event counts start from zero on every call
+  if (cudaMemsetAsync(edep, 0, sizeof(double) * n_events * c->nsub, st) != cudaSuccess ||
+      cudaMemsetAsync(escape_E, 0, sizeof(double) * n_events, st) != cudaSuccess ||
+      cudaMemsetAsync(base + kStaticEvliveOff, 0, sizeof(unsigned) * n_events, st) != cudaSuccess)
+    return GV_ERR_CUDA;
+  DevState<float> s = make_state<float>(c);
+  unsigned char *qp = base + kStaticQueueOff;
+  for (int par = 0; par < 2; ++par)
+    for (int q = 0; q < 3; ++q) s.q[par][q] = carve_static(qp);
+  s.capacity = static_cast<unsigned long long>(kStaticCap);
+  s.ctl = reinterpret_cast<Ctl *>(base + kStaticCtlOff);
+  s.mode = GV_BATCHED;
+  s.low_water = static_cast<unsigned long long>(kStaticCap / 4);
+  s.batch = std::min<unsigned long long>(s.batch, 64);
+  s.max_in_flight = 64;  // ~65k live tracks hold some 64 showers of 10 GeV in Pb
+  s.prim = prim;
+  s.order = nullptr;
+  s.n_prim = static_cast<unsigned>(n);
+  s.n_events = static_cast<unsigned>(n_events);
+  s.edep = edep;
+  s.cell = nullptr;
+  s.escape = escape_E;
+  s.evcnt = nullptr;
+  s.evlive = reinterpret_cast<unsigned *>(base + kStaticEvliveOff);
+  s.seed_lo = static_cast<unsigned>(seed);
+  s.seed_hi = static_cast<unsigned>(seed >> 32);
+  DevState<float> *S = reinterpret_cast<DevState<float> *>(base + kStaticStateOff);
+  static_begin_kernel<<<1, 1, 0, st>>>(s, S);
+  if (cudaGetLastError() != cudaSuccess) return GV_ERR_CUDA;
+  int between = 1;
+  for (;;) {
+    for (int i = 0; i < 2 * between; ++i)
+      step_kernel<float, false><<<grid, c->cfg.block_size, smem, st>>>(S, i & 1);
+    if (cudaGetLastError() != cudaSuccess) return GV_ERR_CUDA;
+    if (cudaMemcpyAsync(c->h_ctl, s.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return GV_ERR_CUDA;
+    if (c->h_ctl->done) break;
+    between = std::min(between * 2, 32);
+  }
+  for (int i = 0; i < 16; ++i) counters[i] = c->h_ctl->counters[i];
+  counters[GV_C_GENERATIONS] = c->h_ctl->gen;
+  counters[15] = c->h_ctl->live_peak;
+  return c->h_ctl->status;
+}

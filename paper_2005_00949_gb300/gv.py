@@ -85,6 +85,8 @@ def load():
             lib.gv_strerror.restype = C.c_char_p
             lib.gv_last_launches.argtypes = [vp]
             lib.gv_last_launches.restype = ll
+            lib.gv_transport_static.argtypes = [vp, vp, ll, ll, C.c_ulonglong, vp, vp, vp,
+                                                C.POINTER(C.c_ulonglong)]
             lib.gv_unit_philox.argtypes = [vp, vp, vp, ll, vp]
             lib.gv_unit_xs_lookup.argtypes = [vp, i, i, vp, ll, vp, vp]
             lib.gv_unit_eloss.argtypes = [vp, i, i, vp, vp, ll, vp, vp]

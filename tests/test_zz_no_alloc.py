@@ -1,0 +1,92 @@
+"""gv_transport_static: the transport for callers that cannot let the library
+allocate device memory during the call (frameworks that own a GPU's memory
+through their own pools).  It must give the same showers as gv_transport --
+identical integer histories, deposits equal up to the order of the FP64
+atomic sums -- on consecutive calls that reuse its fixed scratch array, and
+it must leave the device's free memory unchanged.
+
+This file is named so that pytest collects it last.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2005_00949_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available()
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2005_00949_gb300 import gv
+    return torch, gv
+
+
+def _static_call(torch, gv, ctx, wl, seed):
+    """gv_transport_static through the C ABI with device buffers."""
+    dev = torch.device("cuda")
+    prim = torch.from_numpy(wl.primaries.view(np.uint8).copy()).to(dev)
+    edep = torch.full((wl.n_events, ctx.n_subtotal), 7.0, dtype=torch.float64, device=dev)
+    esc = torch.full((wl.n_events,), 7.0, dtype=torch.float64, device=dev)
+    counters = (C.c_ulonglong * 16)()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    rc = ctx.lib.gv_transport_static(ctx.h, prim.data_ptr(), len(wl.primaries), wl.n_events,
+                                     C.c_ulonglong(seed), torch.cuda.current_stream().cuda_stream,
+                                     edep.data_ptr(), esc.data_ptr(), counters)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    return rc, edep.cpu().numpy(), esc.cpu().numpy(), list(counters), free0 - free1
+
+
+def _reference(ctx, wl, seed):
+    return ctx.transport(wl, seed=seed)
+
+
+def test_static_transport_matches_allocating_transport_twice(env):
+    torch, gv = env
+    wl1 = W.pbps_electrons(300, 1000.0)
+    ctx = gv.Context(wl1, gv.gv_default_config(stack_capacity=1 << 21))
+    # second call: other primaries, fewer events, another seed -- what the first
+    # call left in the scratch array must not leak into it
+    wl2 = W.pbps_mixed(120).subset(120)
+    wl2.primaries["E"] = np.minimum(wl2.primaries["E"], 3000.0)
+    for wl, seed in [(wl1, 12345), (wl2, 777)]:
+        # the allocating call first: whatever the driver sets up lazily on a
+        # kernel's first launch is then in place before free memory is read
+        ref = _reference(ctx, wl, seed)
+        rc, edep, esc, cnt, used = _static_call(torch, gv, ctx, wl, seed)
+        assert rc == 0, gv.load().gv_strerror(rc)
+        names = gv.COUNTER_NAMES
+        for i in range(11):  # steps, tracks, pairs, annihilations, escapes
+            assert cnt[i] == ref["counters"][names[i]], (names[i], cnt[i], ref["counters"][names[i]])
+        scale = np.maximum(ref["edep"].sum(1, keepdims=True), 1.0)
+        assert (np.abs(edep - ref["edep"]) / scale).max() < 1e-9
+        assert np.abs(esc - ref["escape"]).max() < 1e-9 * max(1.0, ref["escape"].max())
+        assert used == 0  # the call took no device memory
+
+
+def test_static_transport_rejects_what_it_cannot_hold(env):
+    torch, gv = env
+    wl = W.pbps_electrons(4, 100.0)
+    ctx = gv.Context(wl, gv.gv_default_config(stack_capacity=1 << 16))
+    dev = torch.device("cuda")
+    prim = torch.from_numpy(wl.primaries.view(np.uint8).copy()).to(dev)
+    counters = (C.c_ulonglong * 16)()
+    too_many = (1 << 16) + 1
+    edep = torch.zeros((too_many, ctx.n_subtotal), dtype=torch.float64, device=dev)
+    esc = torch.zeros(too_many, dtype=torch.float64, device=dev)
+    s = torch.cuda.current_stream().cuda_stream
+    assert ctx.lib.gv_transport_static(ctx.h, prim.data_ptr(), 4, too_many, 1, s, edep.data_ptr(),
+                                       esc.data_ptr(), counters) == -1
+    host_edep = np.zeros((4, ctx.n_subtotal))
+    assert ctx.lib.gv_transport_static(ctx.h, prim.data_ptr(), 4, 4, 1, s, host_edep.ctypes.data,
+                                       esc.data_ptr(), counters) == -1
+    ctx64 = gv.Context(wl, gv.gv_default_config(precision=gv.GV_FP64, stack_capacity=1 << 16))
+    assert ctx64.lib.gv_transport_static(ctx64.h, prim.data_ptr(), 4, 4, 1, s, edep.data_ptr(),
+                                         esc.data_ptr(), counters) == -1

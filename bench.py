@@ -121,6 +121,27 @@ def cpu_baseline(wl, budget_events: int | None = None, repeats: int = 3):
             "steps_per_s": steps / best}
 
 
+def comparators(gv, wl, n_one_event):
+    """The same workload through the other forms of the library on this GPU:
+    FP64 everywhere (batched), and the plain one-event-per-launch schedule
+    (FP64 and mixed) on the first `n_one_event` events."""
+    out = {}
+    forms = [("fp64_batched", dict(precision=gv.GV_FP64), wl),
+             ("fp64_one_event_per_launch", dict(precision=gv.GV_FP64, mode=gv.GV_ONE_EVENT_PER_LAUNCH),
+              wl.subset(n_one_event)),
+             ("mixed_one_event_per_launch", dict(mode=gv.GV_ONE_EVENT_PER_LAUNCH), wl.subset(n_one_event))]
+    for name, kw, w in forms:
+        ctx = gv.Context(w, gv.gv_default_config(stack_capacity=1 << 22, **kw))
+        ctx.transport(w)
+        r = ctx.transport(w)
+        ms = r["kernel_ms"]
+        out[name] = {"events": w.n_events, "ms": ms, "events_per_s": w.n_events / (ms / 1e3),
+                     "steps_per_s": r["counters"]["steps"] / (ms / 1e3),
+                     "timing": "CUDA events around the step-kernel graphs (library work stream)"}
+        ctx.close()
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -161,6 +182,9 @@ def main():
     ap.add_argument("--events", type=int, default=N_EVENTS,
                     help="events per step (profiling of small cases only)")
     ap.add_argument("--capacity", type=int, default=1 << 23, help="track queue capacity per type")
+    ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--comparator-events", type=int, default=200,
+                    help="events of the one-event-per-launch comparators")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -286,6 +310,13 @@ def main():
                      "alg_bytes_per_step": 2 * TRACK_BYTES + TRACK_BYTES * sec_per_step},
         "clocks": clk.summary(),
     }
+    c = list(res.counters)
+    line["diagnostics"] = {
+        "generations": c[11], "live_peak": c[15],
+        "geometry_limited_frac": c[12] / max(c[0], 1), "discrete_frac": c[13] / max(c[0], 1),
+        "idle_lane_frac": 1.0 - c[0] / max(c[14], 1)}
+    if not args.no_comparators:
+        line["comparators"] = comparators(gv, wl, args.comparator_events)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line))

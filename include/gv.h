@@ -59,7 +59,12 @@ extern "C" {
 enum {
   GV_C_STEPS = 0, GV_C_STEPS_G, GV_C_STEPS_EM, GV_C_STEPS_EP,
   GV_C_TRK_G, GV_C_TRK_EM, GV_C_TRK_EP, GV_C_PAIR, GV_C_ANNIH,
-  GV_C_EP_ESC, GV_C_UNSCAT, GV_C_GENERATIONS
+  GV_C_EP_ESC, GV_C_UNSCAT, GV_C_GENERATIONS,
+  /* gv_result.counters only: */
+  GV_C_GEOM,        /* steps limited by a boundary */
+  GV_C_DISCRETE,    /* steps ending in a discrete-process choice */
+  GV_C_LANE_SLOTS,  /* 32 x warp iterations of the step loop (idle lanes = slots - steps) */
+  GV_C_LIVE_PEAK    /* largest live-track population of a generation */
 };
 
 /* A material: n_elem elements with atomic number Z, atomic mass A (g/mol) and
@@ -109,7 +114,9 @@ typedef struct {
   long long max_generations;  /* budget; exceeded -> GV_ERR_TIMEOUT */
   int per_event_counts;       /* 1: keep GV_NCOUNT counters per event (slower) */
   int process_sort;           /* 1: re-basket interacting tracks by process in each block */
-  long long max_events_in_flight; /* refill only while fewer events are unfinished (0: no cap) */
+  long long max_events_in_flight; /* refill only while fewer events are unfinished; 0: no cap;
+                                     -1 (default): stack_capacity / (0.15 per MeV of the most
+                                     energetic primary + 64), at least 16 */
 } gv_config;
 
 /* A primary track; layout shared with the seeded input generator. */

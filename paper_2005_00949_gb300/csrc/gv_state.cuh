@@ -40,6 +40,8 @@ struct Ctl {
   int done;
   int pad;
   unsigned ev_started, ev_done;  // events whose live-track count left / returned to zero
+  unsigned max_in_flight;        // refill cap of this call (0: none)
+  unsigned emax_bits;            // largest primary energy (FP32 bits), for the automatic cap
   unsigned long long gen;
   unsigned long long live_peak;
   unsigned long long counters[16];
@@ -56,7 +58,7 @@ template <typename R> struct DevState {
   double *edep, *cell, *escape;
   unsigned long long *evcnt;
   unsigned *evlive;          // live tracks per event (events-in-flight accounting)
-  unsigned max_in_flight;    // 0: no cap
+  int max_in_flight;         // 0: no cap, -1: automatic from the primaries' energies
   unsigned seed_lo, seed_hi;
   int block_size, mode, K_bulk, K_tail;
   unsigned long long tail_threshold, low_water, batch, max_gen;

@@ -68,9 +68,10 @@ __device__ __forceinline__ void set_status(Ctl *ctl, int code) { atomicCAS(&ctl-
 // blocks derive the children's ids.
 template <typename R>
 __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kids<R> &kids, uint32_t &kk,
-                          BlockCnt *bc, int &proc_out, R *u) {
+                          BlockCnt *bc, int &proc_out, R *u, int &lim_out) {
   kids.n = 0;
   proc_out = -1;
+  lim_out = -1;
   const uint32_t k = t.step;
   kk = k;
   const uint32_t key0 = S->seed_lo ^ t.ev, key1 = S->seed_hi;
@@ -107,6 +108,7 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   R s = s_cont < s_geom ? s_cont : s_geom;
   s = s_phys < s ? s_phys : s;
   const int lim = (s_geom == s) ? 0 : (s_phys == s ? 1 : 2);
+  lim_out = lim;
   if (!(s < INF)) {
     atomicAdd(&S->escape[t.ev], static_cast<double>(t.E));
     if (t.type == 2) count(S, bc, t.ev, GV_C_EP_ESC);
@@ -362,9 +364,9 @@ template <typename R> __device__ void plan_next(const DevState<R> *S, int pn) {
       }
     } else if (live < S->low_water || live == 0) {
       inj = rem < S->batch ? rem : static_cast<unsigned>(S->batch);
-      if (S->max_in_flight) {  // events in flight (Sec. 2.1.1): started and not yet finished
+      if (c->max_in_flight) {  // events in flight (Sec. 2.1.1): started and not yet finished
         const unsigned fl = c->ev_started - c->ev_done;
-        const unsigned room = S->max_in_flight > fl ? S->max_in_flight - fl : 0u;
+        const unsigned room = c->max_in_flight > fl ? c->max_in_flight - fl : 0u;
         inj = inj < room ? inj : room;
       }
     }
@@ -377,7 +379,9 @@ template <typename R> __device__ void plan_next(const DevState<R> *S, int pn) {
   c->chunk_end[1] = c->chunk_end[0] + (n1 + B - 1) / B;
   c->chunk_end[2] = c->chunk_end[1] + (n2 + B - 1) / B;
   c->chunk_end[3] = c->chunk_end[2] + (inj + B - 1) / B;
-  c->K = (live + inj < S->tail_threshold) ? S->K_tail : S->K_bulk;
+  // long claims only in the true tail (every primary injected, few tracks
+  // left); a small population at the start grows fastest with short claims
+  c->K = (c->prim_next == S->n_prim && live + inj < S->tail_threshold) ? S->K_tail : S->K_bulk;
   c->cnt[pn ^ 1][0] = c->cnt[pn ^ 1][1] = c->cnt[pn ^ 1][2] = 0;
   c->claim = 0;
   c->blocks_done = 0;
@@ -400,8 +404,27 @@ template <typename R> __global__ void init_kernel(const DevState<R> *S) {
   c->live_peak = 0;
   c->ev_started = 0;
   c->ev_done = 0;
+  if (S->max_in_flight >= 0) {
+    c->max_in_flight = static_cast<unsigned>(S->max_in_flight);
+  } else {  // automatic: ~0.065 live tracks per MeV at the peak of a shower, x2.3
+    const double emax = static_cast<double>(__uint_as_float(c->emax_bits));
+    const double cap = static_cast<double>(S->capacity) / (0.15 * emax + 64.0);
+    c->max_in_flight = static_cast<unsigned>(cap < 16.0 ? 16.0 : (cap > 1e9 ? 1e9 : cap));
+  }
   for (int i = 0; i < 16; ++i) c->counters[i] = 0;
   plan_next(S, 0);
+}
+
+// largest primary energy, for the automatic events-in-flight cap
+template <typename R> __global__ void prim_emax_kernel(const DevState<R> *S) {
+  float m = 0.0f;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < S->n_prim; i += gridDim.x * blockDim.x) {
+    const float e = static_cast<float>(S->prim[i].E_MeV);
+    m = e > m ? e : m;  // NaN and negative energies leave m unchanged
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(&S->ctl->emax_bits, __float_as_uint(m));
 }
 
 // ------------------------------------------------------------------ the kernel
@@ -527,10 +550,10 @@ __global__ void GV_STEP_BOUNDS step_kernel(const DevState<R> *__restrict__ S, in
       Kids<R> kids;
       kids.n = 0;
       uint32_t kstep = 0;
-      int proc = -1;
+      int proc = -1, lim = -1;
       R u[8];
       if (alive) {
-        alive = step_track(V, S, t, kids, kstep, &bc, proc, u) != 0;
+        alive = step_track(V, S, t, kids, kstep, &bc, proc, u, lim) != 0;
         if (!(t.E == t.E) || !(t.z == t.z)) {
           set_status(ctl, GV_ERR_NUMERIC);
           alive = false;
@@ -553,14 +576,19 @@ __global__ void GV_STEP_BOUNDS step_kernel(const DevState<R> *__restrict__ S, in
         if (m) {
           const unsigned mg = __ballot_sync(0xffffffffu, stepped && t.type == 0);
           const unsigned me = __ballot_sync(0xffffffffu, stepped && t.type == 1);
+          const unsigned mx = __ballot_sync(0xffffffffu, stepped && proc >= 0);
+          const unsigned mb = __ballot_sync(0xffffffffu, stepped && lim == 0);
           if ((tid & 31) == 0) {
             atomicAdd(&bc.c[GV_C_STEPS], static_cast<unsigned long long>(__popc(m)));
             if (mg) atomicAdd(&bc.c[GV_C_STEPS_G], static_cast<unsigned long long>(__popc(mg)));
             if (me) atomicAdd(&bc.c[GV_C_STEPS_EM], static_cast<unsigned long long>(__popc(me)));
             const unsigned mp = m & ~(mg | me);
             if (mp) atomicAdd(&bc.c[GV_C_STEPS_EP], static_cast<unsigned long long>(__popc(mp)));
+            if (mx) atomicAdd(&bc.c[GV_C_DISCRETE], static_cast<unsigned long long>(__popc(mx)));
+            if (mb) atomicAdd(&bc.c[GV_C_GEOM], static_cast<unsigned long long>(__popc(mb)));
           }
         }
+        if ((tid & 31) == 0) atomicAdd(&bc.c[GV_C_LANE_SLOTS], 32ull);  // for the idle-lane fraction
       }
       if (SORT) {
         // S1 basketizer: counting sort of this step's interaction requests by
@@ -738,7 +766,7 @@ int validate_cfg(const gv_config &c) {
   if (c.refill_batch < 1 || c.refill_low_water < 0) return GV_ERR_BAD_ARG;
   if (c.generations_per_graph < 2 || c.generations_per_graph % 2 || c.generations_per_graph > 1024)
     return GV_ERR_BAD_ARG;
-  if (c.max_generations < 1 || c.max_events_in_flight < 0) return GV_ERR_BAD_ARG;
+  if (c.max_generations < 1 || c.max_events_in_flight < -1) return GV_ERR_BAD_ARG;
   return GV_OK;
 }
 
@@ -992,18 +1020,23 @@ int run_transport(Ctx *c, const gv_primary *p, long long n, long long n_events, 
   s.escape = c->d_escape;
   s.evcnt = evc ? c->d_evcnt : nullptr;
   s.evlive = c->d_evlive;
-  s.max_in_flight = static_cast<unsigned>(std::min<long long>(c->cfg.max_events_in_flight, 0xffffffffll));
+  s.max_in_flight = static_cast<int>(std::min<long long>(c->cfg.max_events_in_flight, 0x7fffffffll));
   s.seed_lo = static_cast<unsigned>(seed);
   s.seed_hi = static_cast<unsigned>(seed >> 32);
   static thread_local DevState<R> staged;  // pinned copy not needed: synchronous below
   staged = s;
   CK(cudaMemcpyAsync(c->d_state, &staged, sizeof(s), cudaMemcpyHostToDevice, c->stream));
   const DevState<R> *S = reinterpret_cast<const DevState<R> *>(c->d_state);
+  if (s.max_in_flight < 0) {
+    CK(cudaMemsetAsync(&c->d_ctl->emax_bits, 0, sizeof(unsigned), c->stream));
+    if (n > 0) prim_emax_kernel<R><<<static_cast<int>(std::min<long long>((n + 255) / 256, 4 * c->sm_count)), 256, 0,
+                                     c->stream>>>(S);
+  }
   init_kernel<R><<<1, 1, 0, c->stream>>>(S);
   CK(cudaGetLastError());
   int rc = capture_graph<R>(c);
   if (rc) return rc;
-  long long launches = 1;
+  long long launches = (s.max_in_flight < 0 && n > 0) ? 2 : 1;
   int between = 1;
   double kernel_ms = 0.0;
   for (;;) {
@@ -1066,7 +1099,7 @@ int gv_default_config(gv_config *cfg) {
   cfg->max_generations = 1ll << 20;
   cfg->per_event_counts = 0;
   cfg->process_sort = 0;
-  cfg->max_events_in_flight = 4096;
+  cfg->max_events_in_flight = -1;
   return GV_OK;
 }
 
@@ -1307,6 +1340,7 @@ __global__ void static_begin_kernel(DevState<float> s, DevState<float> *dst) {
   c->live_peak = 0;
   c->ev_started = 0;
   c->ev_done = 0;
+  c->max_in_flight = static_cast<unsigned>(s.max_in_flight);
   for (int i = 0; i < 16; ++i) c->counters[i] = 0;
   plan_next(dst, 0);
 }

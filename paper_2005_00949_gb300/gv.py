@@ -25,7 +25,8 @@ GV_BATCHED, GV_ONE_EVENT_PER_LAUNCH = 0, 1
 NCOUNT = 12
 COUNTER_NAMES = ["steps", "steps_gamma", "steps_eminus", "steps_eplus", "tracks_gamma",
                  "tracks_eminus", "tracks_eplus", "n_pair", "n_annih", "eplus_escaped",
-                 "unscattered", "generations", "", "", "", "live_peak"]
+                 "unscattered", "generations", "geom_limited", "discrete", "lane_slots",
+                 "live_peak"]
 
 
 class GvError(RuntimeError):

@@ -117,6 +117,8 @@ typedef struct {
   long long max_events_in_flight; /* refill only while fewer events are unfinished; 0: no cap;
                                      -1 (default): stack_capacity / (0.15 per MeV of the most
                                      energetic primary + 64), at least 16 */
+  int claim_chunks;           /* without process_sort: 1 (default) = every warp claims its own
+                                 32-track chunks from 16 sliced counters; 0 = one claim per block */
 } gv_config;
 
 /* A primary track; layout shared with the seeded input generator. */
@@ -174,7 +176,7 @@ int gv_transport(void *ctx, const gv_primary *p, long long n, long long n_events
  * The context must already exist (gv_setup and gv_build_tables allocate, once)
  * and use GV_MIXED.  All scratch memory -- track queues for 65,536 tracks per
  * particle type, the generation control block, and live-track counts for up
- * to 65,536 events -- sits in one file-scope device array of 25,436,160 bytes
+ * to 65,536 events -- sits in one file-scope device array of 25,440,256 bytes
  * that every GPU holds from the library's first use on it until the process
  * exits.  The first call on a device looks up that array's address; make it
  * before any stream capture.  Every call reuses the array and clears what

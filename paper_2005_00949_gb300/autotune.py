@@ -22,14 +22,15 @@ import time
 from . import gv, workloads as W
 
 SPACE = {
-    "block_size": [128, 256, 512],
-    "blocks_per_sm": [2, 4, 8],
-    "steps_per_claim": [1, 2, 4, 8, 16],
-    "tail_steps_per_claim": [16, 64, 256],
+    "process_sort": [1, 0],
+    "claim_chunks": [0, 1],
+    "block_size": [128, 256],
+    "blocks_per_sm": [2, 3, 4],
+    "steps_per_claim": [1, 2, 3, 4],
+    "tail_steps_per_claim": [4, 8, 16, 32],
     "tail_threshold": [1 << 15, 1 << 17, 1 << 19],
     "refill_low_water": [1 << 19, 1 << 21, 1 << 23],
     "refill_batch": [1 << 8, 1 << 11, 1 << 14],
-    "process_sort": [0, 1],
 }
 
 

@@ -26,9 +26,16 @@ template <typename R> constexpr size_t track_bytes() {
   return 3 * sizeof(double) + 5 * sizeof(R) + sizeof(unsigned long long) + 3 * sizeof(unsigned);
 }
 
+// Claim counters of the work slices, one per 128-byte line.
+constexpr int kNClaim = 16;
+struct alignas(128) ClaimSlot {
+  unsigned n;
+};
+
 // Generation control block.  The last block of every generation writes the
 // plan of the next one; kernels only read it.
 struct Ctl {
+  ClaimSlot claims[kNClaim];
   unsigned cnt[2][3];        // queue fill per buffer parity and type
   unsigned prim_next;        // primaries handed out so far
   unsigned prim_begin, prim_count;
@@ -61,6 +68,8 @@ template <typename R> struct DevState {
   int max_in_flight;         // 0: no cap, -1: automatic from the primaries' energies
   unsigned seed_lo, seed_hi;
   int block_size, mode, K_bulk, K_tail;
+  int chunk;                 // tracks per work chunk: 32 (a warp) or block_size (basketizer)
+  int claim_chunks;          // chunks a warp takes per atomic claim (no basketizer)
   unsigned long long tail_threshold, low_water, batch, max_gen;
   int n_mat;
   unsigned xs_bytes, zb_bytes;  // staged into shared memory

@@ -76,7 +76,10 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   kk = k;
   const uint32_t key0 = S->seed_lo ^ t.ev, key1 = S->seed_hi;
   const uint32_t idlo = static_cast<uint32_t>(t.id), idhi = static_cast<uint32_t>(t.id >> 32);
-  const uint4 r0 = philox4x32_10(make_uint4(idlo, idhi, k, 0u), key0, key1);
+  // counter block 0 is drawn only when the step needs it: a new n_lambda, or
+  // a physics-limited step (process choice and alias uniforms)
+  uint4 r0 = make_uint4(0u, 0u, 0u, 0u);
+  bool have_r0 = false;
   const R tcut = static_cast<R>(V.cut.tcut);
   if (t.E < tcut) {  // PreStep: tracking cut
     deposit(V, S, t.ev, t.sub, t.x, t.y, t.E);
@@ -89,7 +92,11 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   }
   const int mat = V.smat[t.sub];
   // ComputeIntLen
-  if (t.nlam <= R(0)) t.nlam = -m_log(u24<R>(r0.x));
+  if (t.nlam <= R(0)) {
+    r0 = philox4x32_10(make_uint4(idlo, idhi, k, 0u), key0, key1);
+    have_r0 = true;
+    t.nlam = -m_log(u24<R>(r0.x));
+  }
   const V4<R> s4 = lookup(V, mat, t.type, t.E);
   const R sig0 = s4.x, sig1 = s4.y, sig2 = (t.type == 1) ? R(0) : s4.z;
   const R Sig = sig0 + sig1 + sig2;
@@ -166,6 +173,7 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   }
   if (lim != 1) return 1;
   // PostStepActions: process choice, then the final state
+  if (!have_r0) r0 = philox4x32_10(make_uint4(idlo, idhi, k, 0u), key0, key1);
   const R target = u24<R>(r0.y) * Sig;
   int proc = -1;
   R cum = sig0;
@@ -374,7 +382,7 @@ template <typename R> __device__ void plan_next(const DevState<R> *S, int pn) {
   c->prim_begin = c->prim_next;
   c->prim_count = inj;
   c->prim_next += inj;
-  const unsigned B = static_cast<unsigned>(S->block_size);
+  const unsigned B = static_cast<unsigned>(S->chunk);
   c->chunk_end[0] = (n0 + B - 1) / B;
   c->chunk_end[1] = c->chunk_end[0] + (n1 + B - 1) / B;
   c->chunk_end[2] = c->chunk_end[1] + (n2 + B - 1) / B;
@@ -384,6 +392,7 @@ template <typename R> __device__ void plan_next(const DevState<R> *S, int pn) {
   c->K = (c->prim_next == S->n_prim && live + inj < S->tail_threshold) ? S->K_tail : S->K_bulk;
   c->cnt[pn ^ 1][0] = c->cnt[pn ^ 1][1] = c->cnt[pn ^ 1][2] = 0;
   c->claim = 0;
+  for (int r = 0; r < kNClaim; ++r) c->claims[r].n = 0;
   c->blocks_done = 0;
   if (live + inj > c->live_peak) c->live_peak = live + inj;
   if (live + inj > 0) c->gen += 1;
@@ -428,25 +437,22 @@ template <typename R> __global__ void prim_emax_kernel(const DevState<R> *S) {
 }
 
 // ------------------------------------------------------------------ the kernel
-// Register budget: GV_MIN_BLOCKS resident 256-thread blocks per SM (0: up to
-// 512 threads with no residency target).
+// Register budget: GV_MIN_BLOCKS resident 256-thread blocks per SM in FP32
+// (measured best: 3, i.e. 80 registers with a few spills, beats 2 blocks at
+// 102-126 registers); FP64 keeps 2 blocks (128 registers).
 #ifndef GV_MIN_BLOCKS
-#define GV_MIN_BLOCKS 0
+#define GV_MIN_BLOCKS 3
 #endif
-#if GV_MIN_BLOCKS > 0
-#define GV_STEP_BOUNDS __launch_bounds__(256, GV_MIN_BLOCKS)
 #define GV_MAX_BLOCK 256
-#else
-#define GV_STEP_BOUNDS __launch_bounds__(512)
-#define GV_MAX_BLOCK 512
-#endif
 
 template <typename R, bool SORT>
-__global__ void GV_STEP_BOUNDS step_kernel(const DevState<R> *__restrict__ S, int parity) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_MIN_BLOCKS : 2)
+    step_kernel(const DevState<R> *__restrict__ S, int parity) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ View<R> sV;
   __shared__ BlockCnt bc;
   __shared__ unsigned s_chunk, s_end[4], s_pb;
+  __shared__ unsigned s_slice[kNClaim + 1];
   __shared__ int s_K, s_last;
   __shared__ unsigned s_wcnt[SORT ? kNKey : 1][SORT ? 16 : 1];
   __shared__ unsigned s_nreq;
@@ -473,6 +479,8 @@ __global__ void GV_STEP_BOUNDS step_kernel(const DevState<R> *__restrict__ S, in
       sV.inv_node = idst;
       sV.smat = mdst;
       for (int i = 0; i < 4; ++i) s_end[i] = ctl->chunk_end[i];
+      for (int r = 0; r <= kNClaim; ++r)
+        s_slice[r] = static_cast<unsigned>((static_cast<unsigned long long>(s_end[3]) * r) / kNClaim);
       s_pb = ctl->prim_begin;
       s_K = ctl->K;
     }
@@ -484,16 +492,53 @@ __global__ void GV_STEP_BOUNDS step_kernel(const DevState<R> *__restrict__ S, in
   const unsigned cap = static_cast<unsigned>(S->capacity);
   const unsigned n_in[3] = {min(ctl->cnt[in][0], cap), min(ctl->cnt[in][1], cap), min(ctl->cnt[in][2], cap)};
   const unsigned n_prim_gen = ctl->prim_count;
+  int w_slice = 0;
+  {
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    w_slice = static_cast<int>((smid * 4u + ((tid >> 5) & 3u)) % kNClaim);
+  }
   for (;;) {
-    if (tid == 0) s_chunk = atomicAdd(&ctl->claim, 1u);
-    __syncthreads();
-    const unsigned chunk = s_chunk;
-    __syncthreads();
+    // Work claiming: with the basketizer a chunk is one block (its step loop
+    // syncs the block); without it every warp claims its own 32-track chunks
+    // and never waits for the rest of the block.
+    unsigned chunk, idx;
+    if (SORT || S->claim_chunks == 0) {
+      if (tid == 0) s_chunk = atomicAdd(&ctl->claim, 1u);
+      __syncthreads();
+      chunk = s_chunk;
+      __syncthreads();
+    } else {
+      // The chunk range is split into kNClaim slices, each with its own
+      // counter in its own cache line: a warp draws from its SM's slice and
+      // moves on when that slice is spent, so no single address takes every
+      // claim of the generation.
+      unsigned c0 = 0;
+      if ((tid & 31) == 0) {
+        c0 = 0xffffffffu;
+        for (int k = 0; k < kNClaim; ++k) {
+          const int r = (w_slice + k) % kNClaim;
+          const unsigned lo = s_slice[r], hi = s_slice[r + 1];
+          if (lo >= hi) continue;
+          const unsigned c = lo + atomicAdd(&ctl->claims[r].n, 1u);
+          if (c < hi) {
+            c0 = c;
+            w_slice = r;
+            break;
+          }
+        }
+      }
+      chunk = __shfl_sync(0xffffffffu, c0, 0);
+      if (chunk == 0xffffffffu) break;
+    }
     if (chunk >= s_end[3]) break;
     int qsel = 0;
     while (chunk >= s_end[qsel]) ++qsel;
-    const unsigned first = (chunk - (qsel ? s_end[qsel - 1] : 0u)) * blockDim.x;
-    const unsigned idx = first + tid;
+    {
+      const bool per_block = SORT || S->claim_chunks == 0;
+      const unsigned csize = per_block ? blockDim.x : 32u;
+      idx = (chunk - (qsel ? s_end[qsel - 1] : 0u)) * csize + (per_block ? tid : (tid & 31));
+    }
     Trk<R> t;
     bool alive = false;
     if (qsel < 3) {
@@ -767,6 +812,7 @@ int validate_cfg(const gv_config &c) {
   if (c.generations_per_graph < 2 || c.generations_per_graph % 2 || c.generations_per_graph > 1024)
     return GV_ERR_BAD_ARG;
   if (c.max_generations < 1 || c.max_events_in_flight < -1) return GV_ERR_BAD_ARG;
+  if (c.claim_chunks < 0 || c.claim_chunks > 1) return GV_ERR_BAD_ARG;
   return GV_OK;
 }
 
@@ -902,6 +948,8 @@ template <typename R> DevState<R> make_state(Ctx *c) {
   s.capacity = static_cast<unsigned long long>(c->cfg.stack_capacity);
   s.ctl = c->d_ctl;
   s.block_size = c->cfg.block_size;
+  s.chunk = (c->cfg.process_sort || c->cfg.claim_chunks == 0) ? c->cfg.block_size : 32;
+  s.claim_chunks = c->cfg.claim_chunks;
   s.mode = c->cfg.mode;
   s.K_bulk = c->cfg.steps_per_claim;
   s.K_tail = c->cfg.tail_steps_per_claim;
@@ -1087,10 +1135,12 @@ int gv_default_config(gv_config *cfg) {
   if (!cfg) return GV_ERR_BAD_ARG;
   cfg->precision = GV_MIXED;
   cfg->mode = GV_BATCHED;
+  // measured on 2000 x 10 GeV e- in Pb/polystyrene (GB300): the basketizing
+  // kernel with block claims, 3 blocks of 256 per SM, short claims
   cfg->block_size = 256;
-  cfg->blocks_per_sm = 4;
+  cfg->blocks_per_sm = 3;
   cfg->steps_per_claim = 2;
-  cfg->tail_steps_per_claim = 16;
+  cfg->tail_steps_per_claim = 8;
   cfg->tail_threshold = 100000;
   cfg->stack_capacity = 1ll << 23;
   cfg->refill_low_water = 1ll << 21;
@@ -1098,8 +1148,9 @@ int gv_default_config(gv_config *cfg) {
   cfg->generations_per_graph = 16;
   cfg->max_generations = 1ll << 20;
   cfg->per_event_counts = 0;
-  cfg->process_sort = 0;
+  cfg->process_sort = 1;
   cfg->max_events_in_flight = -1;
+  cfg->claim_chunks = 0;
   return GV_OK;
 }
 
@@ -1270,11 +1321,11 @@ namespace {
 constexpr long long kStaticCap = 1 << 16;         // tracks per particle type and buffer
 constexpr long long kStaticMaxEvents = 1 << 16;   // events per call
 constexpr size_t kStaticCtlOff = 0;
-constexpr size_t kStaticStateOff = 1024;
-constexpr size_t kStaticEvliveOff = 8192;
+constexpr size_t kStaticStateOff = 4096;
+constexpr size_t kStaticEvliveOff = 12288;
 constexpr size_t kStaticQueueOff = kStaticEvliveOff + sizeof(unsigned) * kStaticMaxEvents;
 constexpr size_t kStaticQueueBytes = 6 * static_cast<size_t>(kStaticCap) * track_bytes<float>();
-constexpr size_t kStaticBytes = kStaticQueueOff + kStaticQueueBytes;  // 25,436,160 bytes
+constexpr size_t kStaticBytes = kStaticQueueOff + kStaticQueueBytes;  // 25,440,256 bytes
 static_assert(sizeof(Ctl) <= kStaticStateOff - kStaticCtlOff, "control block does not fit");
 static_assert(sizeof(DevState<float>) <= kStaticEvliveOff - kStaticStateOff, "state does not fit");
 static_assert(kStaticCap % 64 == 0, "queue arrays must stay 256-byte aligned");
@@ -1383,6 +1434,8 @@ extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long 
   s.capacity = static_cast<unsigned long long>(kStaticCap);
   s.ctl = reinterpret_cast<Ctl *>(base + kStaticCtlOff);
   s.mode = GV_BATCHED;
+  s.chunk = c->cfg.block_size;  // the non-basketizing kernel, one claim per block
+  s.claim_chunks = 0;
   s.low_water = static_cast<unsigned long long>(kStaticCap / 4);
   s.batch = std::min<unsigned long long>(s.batch, 64);
   s.max_in_flight = 64;  // ~65k live tracks hold some 64 showers of 10 GeV in Pb

@@ -121,13 +121,17 @@ typedef struct {
                                  32-track chunks from 16 sliced counters; 0 = one claim per block */
 } gv_config;
 
-/* A primary track; layout shared with the seeded input generator. */
+/* A primary track; layout shared with the seeded input generator.  Its random
+ * streams are keyed by (seed, event) and counted from its track id, so an
+ * event's result does not depend on the order of the array or on how events
+ * are split between calls or GPUs (the per-track streams of Sec. 5.1). */
 typedef struct {
   int type;
   double E_MeV;
   double x, y, z;   /* must lie inside the box (z in [0, Z_total]) */
   double u, v, w;   /* unit direction */
   unsigned event;   /* event index, < n_events */
+  unsigned id;      /* track id of the primary within its event (0, 1, ...; distinct per event) */
 } gv_primary;
 
 /* Results of one gv_transport call.  Buffers are caller-owned, host or device,

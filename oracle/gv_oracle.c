@@ -981,7 +981,7 @@ static void run_event(const job_t *J, long ev, ostack *st) {
     t.pos[0] = p->x; t.pos[1] = p->y; t.pos[2] = p->z;
     t.dir[0] = p->u; t.dir[1] = p->v; t.dir[2] = p->w;
     t.nlam = -1.0;
-    t.id = (uint64_t)i;
+    t.id = (uint64_t)p->id;
     t.step = 0;
     t.sub = or_locate(c, p->z, p->w);
     t.primary = 1;

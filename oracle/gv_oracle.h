@@ -82,6 +82,7 @@ typedef struct {
   double x, y, z;      /* cm */
   double u, v, w;      /* unit direction */
   uint32_t event;
+  uint32_t id;         /* track id of the primary within its event */
 } or_primary;
 
 typedef struct or_ctx or_ctx;

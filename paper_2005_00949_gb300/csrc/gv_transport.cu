@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_MIN_BLOCKS : 2)
       t.x = p.x; t.y = p.y; t.z = p.z;
       t.u = static_cast<R>(p.u); t.v = static_cast<R>(p.v); t.w = static_cast<R>(p.w);
       t.nlam = R(-1);
-      t.id = pi;
+      t.id = p.id;
       t.ev = p.event;
       t.step = 0;
       t.flags = kFlagPrimary;

@@ -24,10 +24,11 @@ P_ALL = P_COMPTON | P_PHOTO | P_PAIR | P_BREM | P_IONI | P_ANNIH
 
 DEFAULT_SEED = 0x6765616E7456  # "geantV"
 
-# primary record, laid out like the C struct of both libraries (natural alignment)
+# primary record, laid out like the C struct of both libraries (natural alignment);
+# `id` is the primary's ordinal within its event
 PRIMARY_DTYPE = np.dtype(
     [("type", "<i4"), ("E", "<f8"), ("x", "<f8"), ("y", "<f8"), ("z", "<f8"),
-     ("u", "<f8"), ("v", "<f8"), ("w", "<f8"), ("event", "<u4")],
+     ("u", "<f8"), ("v", "<f8"), ("w", "<f8"), ("event", "<u4"), ("id", "<u4")],
     align=True,
 )
 

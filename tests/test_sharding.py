@@ -1,0 +1,66 @@
+"""Multi-rank event sharding on CPU (gloo, world size 2): each rank transports
+its event range with the FP64 oracle, the tallies are gathered, and the result
+equals the single-process transport exactly (per-event random streams)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_2005_00949_gb300 import sharding, workloads as W
+
+
+def test_shard_ranges_partition_the_events():
+    for n in [0, 1, 7, 100, 2001]:
+        for world in [1, 2, 3, 8]:
+            r = [sharding.shard_range(n, k, world) for k in range(world)]
+            assert r[0][0] == 0 and r[-1][1] == n
+            assert all(a[1] == b[0] for a, b in zip(r, r[1:]))
+            sizes = [hi - lo for lo, hi in r]
+            assert max(sizes) - min(sizes) <= 1
+    with pytest.raises(ValueError):
+        sharding.shard_range(10, 2, 2)
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    import oracle
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        wl = W.wsi_cells(9, 2000.0)
+        shard, lo, hi = sharding.shard_workload(wl, rank, world)
+        res = oracle.Oracle(shard).transport(n_threads=2)
+        full = sharding.gather_tallies(dist, res, lo, hi)
+        if rank == 0:
+            q.put({k: v for k, v in full.items()})
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_transport_equals_single_process(oracle_mod):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    full = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    wl = W.wsi_cells(9, 2000.0)
+    ref = oracle_mod.Oracle(wl).transport(n_threads=2)
+    assert np.array_equal(full["edep"], ref["edep"])
+    assert np.array_equal(full["escape"], ref["escape"])
+    assert np.array_equal(full["counts"], ref["counts"])
+    assert np.allclose(full["cell"], ref["cell"], rtol=1e-12, atol=1e-12)

@@ -119,6 +119,8 @@ typedef struct {
                                      energetic primary + 64), at least 16 */
   int claim_chunks;           /* without process_sort: 1 (default) = every warp claims its own
                                  32-track chunks from 16 sliced counters; 0 = one claim per block */
+  int along_steps;            /* with process_sort: steps a track may take without a discrete
+                                 interaction before its block baskets the interactions (1..64) */
 } gv_config;
 
 /* A primary track; layout shared with the seeded input generator.  Its random

@@ -438,10 +438,10 @@ template <typename R> __global__ void prim_emax_kernel(const DevState<R> *S) {
 
 // ------------------------------------------------------------------ the kernel
 // Register budget: GV_MIN_BLOCKS resident 256-thread blocks per SM in FP32
-// (measured best: 3, i.e. 80 registers with a few spills, beats 2 blocks at
-// 102-126 registers); FP64 keeps 2 blocks (128 registers).
+// (measured: with the along-step loop 2 blocks at up to 128 registers beat
+// 3 blocks at 80 registers, which spill ~700 bytes); FP64 keeps 2 blocks.
 #ifndef GV_MIN_BLOCKS
-#define GV_MIN_BLOCKS 3
+#define GV_MIN_BLOCKS 2
 #endif
 #define GV_MAX_BLOCK 256
 
@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_MIN_BLOCKS : 2)
   __shared__ unsigned s_slice[kNClaim + 1];
   __shared__ int s_K, s_last;
   __shared__ unsigned s_wcnt[SORT ? kNKey : 1][SORT ? 16 : 1];
-  __shared__ unsigned s_nreq;
+  __shared__ unsigned s_walive[SORT ? 16 : 1];
   Ctl *ctl = S->ctl;
   const int tid = threadIdx.x;
   if (ctl->done) return;  // uniform: nothing planned for this generation
@@ -586,62 +586,73 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_MIN_BLOCKS : 2)
     }
     const int K = s_K;
     for (int kk = 0; kk < K; ++kk) {
-      if (SORT) {
-        if (!__syncthreads_or(alive)) break;  // block-uniform: the basketizer syncs
-      } else if (!__any_sync(0xffffffffu, alive)) {
-        break;
-      }
+      // (with the basketizer the block leaves the loop together, after the
+      // count barrier below shows that no lane was alive)
+      if (!SORT && !__any_sync(0xffffffffu, alive)) break;
       const bool was_alive = alive;
       Kids<R> kids;
       kids.n = 0;
       uint32_t kstep = 0;
       int proc = -1, lim = -1;
       R u[8];
-      if (alive) {
+      // Along-step part.  With the basketizer a lane keeps stepping (boundary-
+      // and continuous-limited steps need no final state) until its track is
+      // due a discrete interaction, ends, or has taken along_steps steps; the
+      // block then baskets the interactions.  Step tallies stay per lane and
+      // are summed per warp afterwards.
+      unsigned n_st = 0, n_geom = 0, n_iter = 0;
+      const int inner = SORT ? S->along_steps : 1;
+      for (int m = 0; m < inner && alive && proc < 0; ++m) {
+        ++n_iter;
+        const uint32_t before = t.step;
         alive = step_track(V, S, t, kids, kstep, &bc, proc, u, lim) != 0;
         if (!(t.E == t.E) || !(t.z == t.z)) {
           set_status(ctl, GV_ERR_NUMERIC);
           alive = false;
           proc = -1;
         }
-        if (!SORT && proc >= 0) {  // final state in place (warp-divergent across processes)
-          R d[3] = {t.u, t.v, t.w};
-          const int r = final_state(V, S, &bc, t.type, proc, t.E, d, u, kids, t.ev, t.sub, t.x, t.y);
-          if (r >= 0) {
-            t.u = d[0]; t.v = d[1]; t.w = d[2];
-            t.flags |= kFlagInteracted;
-            alive = r != 0;
-          }
+        if (t.step != before) {
+          ++n_st;
+          n_geom += lim == 0 ? 1u : 0u;
+        }
+      }
+      if (!SORT && alive && proc >= 0) {  // final state in place (warp-divergent across processes)
+        R d[3] = {t.u, t.v, t.w};
+        const int r = final_state(V, S, &bc, t.type, proc, t.E, d, u, kids, t.ev, t.sub, t.x, t.y);
+        if (r >= 0) {
+          t.u = d[0]; t.v = d[1]; t.w = d[2];
+          t.flags |= kFlagInteracted;
+          alive = r != 0;
         }
       }
       push_kids(S, out, parent_of(t), kids, kstep, &bc);
       {  // step counters, one shared-memory atomic per warp and kind
-        const bool stepped = was_alive && t.step != kstep;
-        const unsigned m = __ballot_sync(0xffffffffu, stepped);
-        if (m) {
-          const unsigned mg = __ballot_sync(0xffffffffu, stepped && t.type == 0);
-          const unsigned me = __ballot_sync(0xffffffffu, stepped && t.type == 1);
-          const unsigned mx = __ballot_sync(0xffffffffu, stepped && proc >= 0);
-          const unsigned mb = __ballot_sync(0xffffffffu, stepped && lim == 0);
+        const unsigned wst = __reduce_add_sync(0xffffffffu, n_st);
+        const unsigned wiq = __reduce_max_sync(0xffffffffu, n_iter);
+        if (wst) {
+          const unsigned wg = __reduce_add_sync(0xffffffffu, t.type == 0 ? n_st : 0u);
+          const unsigned we = __reduce_add_sync(0xffffffffu, t.type == 1 ? n_st : 0u);
+          const unsigned wx = __reduce_add_sync(0xffffffffu, (n_st && proc >= 0) ? 1u : 0u);
+          const unsigned wb = __reduce_add_sync(0xffffffffu, n_geom);
           if ((tid & 31) == 0) {
-            atomicAdd(&bc.c[GV_C_STEPS], static_cast<unsigned long long>(__popc(m)));
-            if (mg) atomicAdd(&bc.c[GV_C_STEPS_G], static_cast<unsigned long long>(__popc(mg)));
-            if (me) atomicAdd(&bc.c[GV_C_STEPS_EM], static_cast<unsigned long long>(__popc(me)));
-            const unsigned mp = m & ~(mg | me);
-            if (mp) atomicAdd(&bc.c[GV_C_STEPS_EP], static_cast<unsigned long long>(__popc(mp)));
-            if (mx) atomicAdd(&bc.c[GV_C_DISCRETE], static_cast<unsigned long long>(__popc(mx)));
-            if (mb) atomicAdd(&bc.c[GV_C_GEOM], static_cast<unsigned long long>(__popc(mb)));
+            atomicAdd(&bc.c[GV_C_STEPS], static_cast<unsigned long long>(wst));
+            if (wg) atomicAdd(&bc.c[GV_C_STEPS_G], static_cast<unsigned long long>(wg));
+            if (we) atomicAdd(&bc.c[GV_C_STEPS_EM], static_cast<unsigned long long>(we));
+            if (wst - wg - we) atomicAdd(&bc.c[GV_C_STEPS_EP], static_cast<unsigned long long>(wst - wg - we));
+            if (wx) atomicAdd(&bc.c[GV_C_DISCRETE], static_cast<unsigned long long>(wx));
+            if (wb) atomicAdd(&bc.c[GV_C_GEOM], static_cast<unsigned long long>(wb));
           }
         }
-        if ((tid & 31) == 0) atomicAdd(&bc.c[GV_C_LANE_SLOTS], 32ull);  // for the idle-lane fraction
+        if ((tid & 31) == 0 && wiq) atomicAdd(&bc.c[GV_C_LANE_SLOTS], 32ull * wiq);  // idle-lane fraction
       }
       if (SORT) {
         // S1 basketizer: counting sort of this step's interaction requests by
-        // (type, process) -- warp ballots, a block prefix sum, one slot each --
-        // so every warp runs a single final-state model.
+        // (type, process) -- warp ballots, a prefix sum over keys and warps,
+        // one slot each -- so every warp runs a single final-state model.
+        // Three block barriers per step: counts, requests, results.
         IReq<R> *req = reinterpret_cast<IReq<R> *>(smem + S->smem_req_off);
         const int key = (alive && proc >= 0) ? t.type * 3 + proc : -1;
-        const int lane = tid & 31, warp = tid >> 5;
+        const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
         unsigned rank = 0;
 #pragma unroll
         for (int k = 0; k < kNKey; ++k) {
@@ -649,20 +660,31 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_MIN_BLOCKS : 2)
           if (lane == 0) s_wcnt[k][warp] = __popc(m);
           if (key == k) rank = __popc(m & ((1u << lane) - 1u));
         }
+        const unsigned ma = __ballot_sync(0xffffffffu, was_alive);
+        if (lane == 0) s_walive[warp] = ma;
         __syncthreads();
-        if (tid == 0) {
-          const int nw = blockDim.x >> 5;
-          unsigned run = 0;
-          for (int k = 0; k < kNKey; ++k)
-            for (int w = 0; w < nw; ++w) {
-              const unsigned c = s_wcnt[k][w];
-              s_wcnt[k][w] = run;
-              run += c;
-            }
-          s_nreq = run;
+        unsigned any = 0;
+        for (int w = 0; w < nw; ++w) any |= s_walive[w];
+        if (!any) break;  // uniform: no lane of the block was alive this step
+        // lane k < kNKey: requests of key k in the block and in warps before this one
+        unsigned ck = 0, part = 0;
+        if (lane < kNKey) {
+          for (int w = 0; w < nw; ++w) {
+            const unsigned c = s_wcnt[lane][w];
+            ck += c;
+            part += (w < warp) ? c : 0u;
+          }
         }
-        __syncthreads();
-        const unsigned slot = key >= 0 ? s_wcnt[key][warp] + rank : 0u;
+        unsigned incl = ck;
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) {
+          const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const unsigned start = incl - ck + part;  // first slot of key `lane` for this warp
+        const unsigned nreq = __shfl_sync(0xffffffffu, incl, kNKey - 1);
+        const unsigned mine = __shfl_sync(0xffffffffu, start, key >= 0 ? key : 0);
+        const unsigned slot = key >= 0 ? mine + rank : 0u;
         if (key >= 0) {
           IReq<R> &q = req[slot];
           q.x = t.x; q.y = t.y; q.z = t.z;
@@ -680,7 +702,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_MIN_BLOCKS : 2)
         kb.n = 0;
         Parent par;
         uint32_t pk = 0;
-        if (static_cast<unsigned>(tid) < s_nreq) {
+        if (static_cast<unsigned>(tid) < nreq) {
           IReq<R> &q = req[tid];
           R uu[8] = {R(0), R(0), q.u[0], q.u[1], q.u[2], q.u[3], q.u[4], q.u[5]};
           R d[3] = {q.d0, q.d1, q.d2};
@@ -813,6 +835,7 @@ int validate_cfg(const gv_config &c) {
     return GV_ERR_BAD_ARG;
   if (c.max_generations < 1 || c.max_events_in_flight < -1) return GV_ERR_BAD_ARG;
   if (c.claim_chunks < 0 || c.claim_chunks > 1) return GV_ERR_BAD_ARG;
+  if (c.along_steps < 1 || c.along_steps > 64) return GV_ERR_BAD_ARG;
   return GV_OK;
 }
 
@@ -950,6 +973,7 @@ template <typename R> DevState<R> make_state(Ctx *c) {
   s.block_size = c->cfg.block_size;
   s.chunk = (c->cfg.process_sort || c->cfg.claim_chunks == 0) ? c->cfg.block_size : 32;
   s.claim_chunks = c->cfg.claim_chunks;
+  s.along_steps = c->cfg.along_steps;
   s.mode = c->cfg.mode;
   s.K_bulk = c->cfg.steps_per_claim;
   s.K_tail = c->cfg.tail_steps_per_claim;
@@ -1136,10 +1160,11 @@ int gv_default_config(gv_config *cfg) {
   cfg->precision = GV_MIXED;
   cfg->mode = GV_BATCHED;
   // measured on 2000 x 10 GeV e- in Pb/polystyrene (GB300): the basketizing
-  // kernel with block claims, 3 blocks of 256 per SM, short claims
+  // kernel with block claims, 2 blocks of 256 per SM, up to 4 along-steps per
+  // basket round, one round per claim
   cfg->block_size = 256;
-  cfg->blocks_per_sm = 3;
-  cfg->steps_per_claim = 2;
+  cfg->blocks_per_sm = 2;
+  cfg->steps_per_claim = 1;
   cfg->tail_steps_per_claim = 8;
   cfg->tail_threshold = 100000;
   cfg->stack_capacity = 1ll << 23;
@@ -1151,6 +1176,7 @@ int gv_default_config(gv_config *cfg) {
   cfg->process_sort = 1;
   cfg->max_events_in_flight = -1;
   cfg->claim_chunks = 0;
+  cfg->along_steps = 4;
   return GV_OK;
 }
 

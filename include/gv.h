@@ -121,6 +121,13 @@ typedef struct {
                                  32-track chunks from 16 sliced counters; 0 = one claim per block */
   int along_steps;            /* with process_sort: steps a track may take without a discrete
                                  interaction before its block baskets the interactions (1..64) */
+  int scoring;                /* energy tallies: 0 (default) = one FP64 atomic per deposit;
+                                 1 = a lane merges consecutive deposits to the same (event,
+                                 sub-slab) in a compensated sum, and after every step round its
+                                 warp adds equal keys together before one FP64 atomic per key */
+  int l2_persist;             /* 1: gv_transport's step kernels read the alias tables through a persisting
+                                 L2 access-policy window; the context's persisting L2 set-aside is
+                                 raised to the tables' size and restored by gv_destroy */
 } gv_config;
 
 /* A primary track; layout shared with the seeded input generator.  Its random

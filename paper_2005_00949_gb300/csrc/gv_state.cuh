@@ -71,6 +71,7 @@ template <typename R> struct DevState {
   int chunk;                 // tracks per work chunk: 32 (a warp) or block_size (basketizer)
   int claim_chunks;          // chunks a warp takes per atomic claim (no basketizer)
   int along_steps;           // basketizer: steps per lane before the block basket
+  int scoring;               // 0 direct atomics, 1 warp-merged (selects the kernel)
   unsigned long long tail_threshold, low_water, batch, max_gen;
   int n_mat;
   unsigned xs_bytes, zb_bytes;  // staged into shared memory

@@ -28,11 +28,45 @@ struct BlockCnt {
   unsigned long long c[16];
 };
 
+// Scoring (SteppingActions, Sec. 3.8.1).  A lane keeps one pending
+// (event, sub-slab) deposit: consecutive deposits of its track to the same sub-slab merge with a
+// compensated (Kahan) sum in R; a deposit to another sub-slab flushes the
+// pending one with an FP64 atomic; at the end of every round the warp groups
+// its pending deposits by key (__match_any_sync), sums each group with a
+// compensated shuffle reduction, and one lane per group adds it to the FP64
+// tally.  pd == nullptr scores directly.
+constexpr unsigned long long kNoKey = ~0ull;
+
+template <typename R> struct Pending {
+  unsigned long long key;
+  R sum, comp;
+};
+
+template <typename R> __device__ __forceinline__ void kahan_add(R &sum, R &comp, R v) {
+  const R y = v - comp;
+  const R t = sum + y;
+  comp = (t - sum) - y;
+  sum = t;
+}
+
 template <typename R>
 __device__ __forceinline__ void deposit(const View<R> &V, const DevState<R> *S, unsigned ev, int sub, double px,
-                                        double py, R dE) {
+                                        double py, R dE, Pending<R> *pd = nullptr) {
   if (!(dE != R(0)) || sub < 0) return;
-  atomicAdd(&S->edep[static_cast<size_t>(ev) * V.geo.nsub + sub], static_cast<double>(dE));
+  const unsigned long long key = static_cast<unsigned long long>(ev) * V.geo.nsub + sub;
+  if (pd) {
+    if (pd->key == key) {
+      kahan_add(pd->sum, pd->comp, dE);
+    } else {
+      if (pd->key != kNoKey)
+        atomicAdd(&S->edep[pd->key], static_cast<double>(pd->sum) - static_cast<double>(pd->comp));
+      pd->key = key;
+      pd->sum = dE;
+      pd->comp = R(0);
+    }
+  } else {
+    atomicAdd(&S->edep[key], static_cast<double>(dE));
+  }
   if (S->cell) {
     const GeoConst &g = V.geo;
     const int layer = sub / g.nsub_layer;
@@ -42,6 +76,25 @@ __device__ __forceinline__ void deposit(const View<R> &V, const DevState<R> *S, 
     iy = iy < 0 ? 0 : (iy >= g.ny ? g.ny - 1 : iy);
     atomicAdd(&S->cell[(static_cast<size_t>(layer) * g.nx + ix) * g.ny + iy], static_cast<double>(dE));
   }
+}
+
+// Warp flush of the pending deposits (all 32 lanes, converged).
+template <typename R> __device__ __forceinline__ void warp_flush(const DevState<R> *S, Pending<R> &p) {
+  const unsigned m = __match_any_sync(0xffffffffu, p.key);
+  if (p.key != kNoKey) {
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    const R v = p.sum - p.comp;
+    R acc = v, comp = R(0);
+    unsigned rest = m & ~(1u << leader);
+    while (rest) {  // every lane of the group runs the same iterations
+      const int src = __ffs(rest) - 1;
+      rest &= rest - 1u;
+      const R w = __shfl_sync(m, v, src);
+      if (lane == leader) kahan_add(acc, comp, w);
+    }
+    if (lane == leader) atomicAdd(&S->edep[p.key], static_cast<double>(acc) - static_cast<double>(comp));
+  }
+  p.key = kNoKey;
 }
 
 template <typename R>
@@ -68,7 +121,7 @@ __device__ __forceinline__ void set_status(Ctl *ctl, int code) { atomicCAS(&ctl-
 // blocks derive the children's ids.
 template <typename R>
 __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kids<R> &kids, uint32_t &kk,
-                          BlockCnt *bc, int &proc_out, R *u, int &lim_out) {
+                          BlockCnt *bc, int &proc_out, R *u, int &lim_out, Pending<R> *pd) {
   kids.n = 0;
   proc_out = -1;
   lim_out = -1;
@@ -82,7 +135,7 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   bool have_r0 = false;
   const R tcut = static_cast<R>(V.cut.tcut);
   if (t.E < tcut) {  // PreStep: tracking cut
-    deposit(V, S, t.ev, t.sub, t.x, t.y, t.E);
+    deposit(V, S, t.ev, t.sub, t.x, t.y, t.E, pd);
     if (t.type == 2) {
       const uint4 r1 = philox4x32_10(make_uint4(idlo, idhi, k, 1u), key0, key1);
       at_rest(kids, u24<R>(r1.z), u24<R>(r1.w));
@@ -148,10 +201,10 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   // AlongStepAction
   if (charged) {
     const R Ep = eloss(V, mat, t.type, t.E, s);
-    deposit(V, S, t.ev, pre_sub, mx, my, t.E - Ep);
+    deposit(V, S, t.ev, pre_sub, mx, my, t.E - Ep, pd);
     t.E = Ep;
     if (t.E < tcut) {
-      deposit(V, S, t.ev, pre_sub, t.x, t.y, t.E);
+      deposit(V, S, t.ev, pre_sub, t.x, t.y, t.E, pd);
       if (t.type == 2) {
         const uint4 r1 = philox4x32_10(make_uint4(idlo, idhi, k, 1u), key0, key1);
         at_rest(kids, u24<R>(r1.z), u24<R>(r1.w));
@@ -203,14 +256,14 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
 template <typename R>
 __device__ __forceinline__ int final_state(const View<R> &V, const DevState<R> *S, BlockCnt *bc, int type, int proc,
                                            R &E, R d[3], const R *u, Kids<R> &kids, unsigned ev, int sub,
-                                           double x, double y) {
+                                           double x, double y, Pending<R> *pd = nullptr) {
   R local;
   int np = 0, na = 0;
   const int r = interact(V, type, proc, E, d, u, kids, local, np, na);
   if (r < 0) return -1;
   if (np) count(S, bc, ev, GV_C_PAIR, np);
   if (na) count(S, bc, ev, GV_C_ANNIH, na);
-  deposit(V, S, ev, sub, x, y, local);
+  deposit(V, S, ev, sub, x, y, local, pd);
   return r;
 }
 
@@ -268,7 +321,7 @@ template <typename R> __device__ __forceinline__ Parent parent_of(const Trk<R> &
   return p;
 }
 
-// S9: append the step's secondaries to the output queues.  Called by all 32
+// PostStepActions: append the step's secondaries to the output queues.  Called by all 32
 // lanes of a converged warp (lanes without secondaries pass kids.n == 0).
 template <typename R>
 __device__ void push_kids(const DevState<R> *S, int out, const Parent &t, const Kids<R> &kids, uint32_t kk,
@@ -445,7 +498,7 @@ template <typename R> __global__ void prim_emax_kernel(const DevState<R> *S) {
 #endif
 #define GV_MAX_BLOCK 256
 
-template <typename R, bool SORT>
+template <typename R, bool SORT, bool MERGE>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_MIN_BLOCKS : 2)
     step_kernel(const DevState<R> *__restrict__ S, int parity) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -498,6 +551,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_MIN_BLOCKS : 2)
     asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
     w_slice = static_cast<int>((smid * 4u + ((tid >> 5) & 3u)) % kNClaim);
   }
+  Pending<R> pend;  // this lane's unflushed deposit (merged scoring)
+  pend.key = kNoKey;
+  pend.sum = R(0);
+  pend.comp = R(0);
+  Pending<R> *const pd = MERGE ? &pend : nullptr;
   for (;;) {
     // Work claiming: with the basketizer a chunk is one block (its step loop
     // syncs the block); without it every warp claims its own 32-track chunks
@@ -605,7 +663,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_MIN_BLOCKS : 2)
       for (int m = 0; m < inner && alive && proc < 0; ++m) {
         ++n_iter;
         const uint32_t before = t.step;
-        alive = step_track(V, S, t, kids, kstep, &bc, proc, u, lim) != 0;
+        alive = step_track(V, S, t, kids, kstep, &bc, proc, u, lim, pd) != 0;
         if (!(t.E == t.E) || !(t.z == t.z)) {
           set_status(ctl, GV_ERR_NUMERIC);
           alive = false;
@@ -618,7 +676,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_MIN_BLOCKS : 2)
       }
       if (!SORT && alive && proc >= 0) {  // final state in place (warp-divergent across processes)
         R d[3] = {t.u, t.v, t.w};
-        const int r = final_state(V, S, &bc, t.type, proc, t.E, d, u, kids, t.ev, t.sub, t.x, t.y);
+        const int r = final_state(V, S, &bc, t.type, proc, t.E, d, u, kids, t.ev, t.sub, t.x, t.y, pd);
         if (r >= 0) {
           t.u = d[0]; t.v = d[1]; t.w = d[2];
           t.flags |= kFlagInteracted;
@@ -626,6 +684,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_MIN_BLOCKS : 2)
         }
       }
       push_kids(S, out, parent_of(t), kids, kstep, &bc);
+      if (MERGE) warp_flush(S, pend);
       {  // step counters, one shared-memory atomic per warp and kind
         const unsigned wst = __reduce_add_sync(0xffffffffu, n_st);
         const unsigned wiq = __reduce_max_sync(0xffffffffu, n_iter);
@@ -646,7 +705,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_MIN_BLOCKS : 2)
         if ((tid & 31) == 0 && wiq) atomicAdd(&bc.c[GV_C_LANE_SLOTS], 32ull * wiq);  // idle-lane fraction
       }
       if (SORT) {
-        // S1 basketizer: counting sort of this step's interaction requests by
+        // Basketizer: counting sort of this step's interaction requests by
         // (type, process) -- warp ballots, a prefix sum over keys and warps,
         // one slot each -- so every warp runs a single final-state model.
         // Three block barriers per step: counts, requests, results.
@@ -730,6 +789,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_MIN_BLOCKS : 2)
       }
       if (was_alive && !alive) track_ended(S, t.ev);
     }
+    if (MERGE) warp_flush(S, pend);  // nothing stays pending past a claim
     push_survivor(S, out, t, alive);
   }
   // flush block counters; the last block plans the next generation
@@ -788,8 +848,10 @@ struct Ctx {
   long long launches = 0;
   int last_status = 0;
   ModelMeta meta[kNModel];
-  size_t xs_bytes = 0, zb_bytes = 0, smem_bytes = 0, req_off = 0;
+  size_t xs_bytes = 0, zb_bytes = 0, smem_bytes = 0, req_off = 0, bins_bytes = 0;
   int grid = 0;
+  // L2 persisting window over the alias bins (config l2_persist)
+  size_t l2_window = 0, l2_old_limit = 0;
 };
 
 #define CK(x)                                  \
@@ -836,6 +898,8 @@ int validate_cfg(const gv_config &c) {
   if (c.max_generations < 1 || c.max_events_in_flight < -1) return GV_ERR_BAD_ARG;
   if (c.claim_chunks < 0 || c.claim_chunks > 1) return GV_ERR_BAD_ARG;
   if (c.along_steps < 1 || c.along_steps > 64) return GV_ERR_BAD_ARG;
+  if (c.scoring < 0 || c.scoring > 1) return GV_ERR_BAD_ARG;
+  if (c.l2_persist < 0 || c.l2_persist > 1) return GV_ERR_BAD_ARG;
   return GV_OK;
 }
 
@@ -908,8 +972,26 @@ template <typename R> int upload_tables(Ctx *c) {
         bins.push_back(b);
       }
   }
-  CK(cudaMalloc(&c->d_bins, bins.size() * sizeof(AliasBin<R>)));
-  CK(cudaMemcpy(c->d_bins, bins.data(), bins.size() * sizeof(AliasBin<R>), cudaMemcpyHostToDevice));
+  c->bins_bytes = bins.size() * sizeof(AliasBin<R>);
+  CK(cudaMalloc(&c->d_bins, c->bins_bytes));
+  CK(cudaMemcpy(c->d_bins, bins.data(), c->bins_bytes, cudaMemcpyHostToDevice));
+  return GV_OK;
+}
+
+// Alias bins are read at random by every interaction; a persisting L2
+// window keeps them resident while the queues stream through L2.  The
+// context's persisting set-aside is raised to the window (if smaller) and put
+// back by gv_destroy.
+int setup_l2_window(Ctx *c) {
+  if (!c->cfg.l2_persist || !c->bins_bytes) return GV_OK;
+  int max_persist = 0, max_window = 0;
+  CK(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, c->device));
+  CK(cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, c->device));
+  const size_t w = std::min(c->bins_bytes, static_cast<size_t>(std::min(max_persist, max_window)));
+  if (w == 0) return GV_OK;  // no persisting L2 on this device: nothing to do
+  CK(cudaDeviceGetLimit(&c->l2_old_limit, cudaLimitPersistingL2CacheSize));
+  if (c->l2_old_limit < w) CK(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, w));
+  c->l2_window = w;
   return GV_OK;
 }
 
@@ -937,9 +1019,20 @@ template <typename R> View<R> make_view(const Ctx *c) {
   return v;
 }
 
+template <typename R> using StepFn = void (*)(const DevState<R> *, int);
+
+// The step kernel compiled for this configuration: basketizer or not, merged
+// or direct scoring.
+template <typename R> StepFn<R> pick_step_kernel(const gv_config &c) {
+  if (c.process_sort) return c.scoring ? step_kernel<R, true, true> : step_kernel<R, true, false>;
+  return c.scoring ? step_kernel<R, false, true> : step_kernel<R, false, false>;
+}
+
 template <typename R> int prepare_device(Ctx *c) {
   CK(cudaSetDevice(c->device));
   int rc = upload_tables<R>(c);
+  if (rc) return rc;
+  rc = setup_l2_window(c);
   if (rc) return rc;
   const long long cap = c->cfg.stack_capacity;
   const size_t per = carve_bytes<R>(cap);
@@ -951,8 +1044,7 @@ template <typename R> int prepare_device(Ctx *c) {
   c->zb_bytes = ((c->nsub + 1) * sizeof(double) + 15) / 16 * 16;
   c->req_off = c->xs_bytes + c->zb_bytes + kInvNodeBytes + (c->nsub + 15) / 16 * 16;
   c->smem_bytes = c->req_off + (c->cfg.process_sort ? sizeof(IReq<R>) * c->cfg.block_size : 0);
-  const void *kern = c->cfg.process_sort ? reinterpret_cast<const void *>(step_kernel<R, true>)
-                                         : reinterpret_cast<const void *>(step_kernel<R, false>);
+  const void *kern = reinterpret_cast<const void *>(pick_step_kernel<R>(c->cfg));
   CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(c->smem_bytes)));
   int occ = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, c->cfg.block_size, c->smem_bytes));
@@ -974,6 +1066,7 @@ template <typename R> DevState<R> make_state(Ctx *c) {
   s.chunk = (c->cfg.process_sort || c->cfg.claim_chunks == 0) ? c->cfg.block_size : 32;
   s.claim_chunks = c->cfg.claim_chunks;
   s.along_steps = c->cfg.along_steps;
+  s.scoring = c->cfg.scoring;
   s.mode = c->cfg.mode;
   s.K_bulk = c->cfg.steps_per_claim;
   s.K_tail = c->cfg.tail_steps_per_claim;
@@ -993,14 +1086,33 @@ template <typename R> int capture_graph(Ctx *c) {
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
   const DevState<R> *S = reinterpret_cast<const DevState<R> *>(c->d_state);
-  for (int i = 0; i < c->cfg.generations_per_graph; ++i) {
-    if (c->cfg.process_sort)
-      step_kernel<R, true><<<c->grid, c->cfg.block_size, c->smem_bytes, c->stream>>>(S, i & 1);
-    else
-      step_kernel<R, false><<<c->grid, c->cfg.block_size, c->smem_bytes, c->stream>>>(S, i & 1);
-  }
+  const StepFn<R> step = pick_step_kernel<R>(c->cfg);
+  for (int i = 0; i < c->cfg.generations_per_graph; ++i)
+    step<<<c->grid, c->cfg.block_size, c->smem_bytes, c->stream>>>(S, i & 1);
   cudaError_t e = cudaStreamEndCapture(c->stream, &g);
   if (e != cudaSuccess) return GV_ERR_CUDA;
+  if (c->l2_window) {  // the window rides on every captured step launch
+    size_t nn = 0;
+    e = cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (e == cudaSuccess && nn) e = cudaGraphGetNodes(g, nodes.data(), &nn);
+    cudaKernelNodeAttrValue v{};
+    v.accessPolicyWindow.base_ptr = c->d_bins;
+    v.accessPolicyWindow.num_bytes = c->l2_window;
+    v.accessPolicyWindow.hitRatio = 1.0f;
+    v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
+      cudaGraphNodeType ty;
+      e = cudaGraphNodeGetType(nodes[i], &ty);
+      if (e == cudaSuccess && ty == cudaGraphNodeTypeKernel)
+        e = cudaGraphKernelNodeSetAttribute(nodes[i], cudaKernelNodeAttributeAccessPolicyWindow, &v);
+    }
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return GV_ERR_CUDA;
+    }
+  }
   e = cudaGraphInstantiate(&c->graph, g, 0);
   cudaGraphDestroy(g);
   return e == cudaSuccess ? GV_OK : GV_ERR_CUDA;
@@ -1177,6 +1289,8 @@ int gv_default_config(gv_config *cfg) {
   cfg->max_events_in_flight = -1;
   cfg->claim_chunks = 0;
   cfg->along_steps = 4;
+  cfg->scoring = 0;
+  cfg->l2_persist = 0;
   return GV_OK;
 }
 
@@ -1277,6 +1391,10 @@ void gv_destroy(void *ctx) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->l2_window) {  // release the persisting lines and the set-aside taken at setup
+    cudaCtxResetPersistingL2Cache();
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, c->l2_old_limit);
+  }
   cudaFree(c->d_xs);
   cudaFree(c->d_inv_node);
   cudaFree(c->d_bins);
@@ -1439,11 +1557,11 @@ extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long 
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t smem = c->req_off;  // tables and geometry; the non-basketizing kernel
-  if (cudaFuncSetAttribute(step_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(step_kernel<float, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess)
     return GV_ERR_CUDA;
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_kernel<float, false>, c->cfg.block_size, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_kernel<float, false, false>, c->cfg.block_size, smem) !=
           cudaSuccess ||
       occ < 1)
     return GV_ERR_CUDA;
@@ -1482,7 +1600,7 @@ extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long 
   int between = 1;
   for (;;) {
     for (int i = 0; i < 2 * between; ++i)
-      step_kernel<float, false><<<grid, c->cfg.block_size, smem, st>>>(S, i & 1);
+      step_kernel<float, false, false><<<grid, c->cfg.block_size, smem, st>>>(S, i & 1);
     if (cudaGetLastError() != cudaSuccess) return GV_ERR_CUDA;
     if (cudaMemcpyAsync(c->h_ctl, s.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)

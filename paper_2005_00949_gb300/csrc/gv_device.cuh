@@ -45,11 +45,22 @@ struct ModelMeta {
 struct GeoConst {
   int nsub, nsub_layer, n_layers, nx, ny;
   double hx, hy, pitch_x, pitch_y;
+  double wx[2], wy[2];  // the x and y walls {-h, +h}
+  float inv_pitch_x, inv_pitch_y;
+  int walls_x, walls_y; // 0: unbounded in that direction
 };
 
 struct CutConst {
   double gcut, ecut, tcut;
   unsigned mask;
+};
+
+// The cuts and the alias grids' constants in R, converted once on the host:
+// on GB300 a conversion between FP64 and FP32 issues on the FP64 pipe,
+// which the FP32 kernels should leave to the position arithmetic.
+template <typename R> struct RConst {
+  R tcut, gcut, ecut, ecut_push;  // ecut_push = max(e- cut, tracking cut)
+  R ln_Elo[kNModel], inv_dl[kNModel], cut[kNModel];
 };
 
 // Read-only view of everything one step needs.
@@ -62,6 +73,7 @@ template <typename R> struct View {
   ModelMeta meta[kNModel];
   GeoConst geo;
   CutConst cut;
+  RConst<R> rc;
 };
 
 // ---------------------------------------------------------------- RNG
@@ -200,7 +212,7 @@ template <typename R> __device__ __forceinline__ R reduced_to_physical(int m, R 
 template <typename R>
 __device__ R alias_sample(const View<R> &V, int m, R E, R ug, R ub, R ui, R *xi_out = nullptr) {
   const ModelMeta &M = V.meta[m];
-  const R l = (m_log(E) - static_cast<R>(M.ln_Elo)) * static_cast<R>(M.inv_dl);
+  const R l = (m_log(E) - V.rc.ln_Elo[m]) * V.rc.inv_dl[m];
   int ie;
   if (l <= R(0)) ie = 0;
   else if (l >= static_cast<R>(M.nE - 1)) ie = M.nE - 1;
@@ -223,36 +235,31 @@ __device__ R alias_sample(const View<R> &V, int m, R E, R ug, R ub, R ui, R *xi_
   const R t = ui * (p0 + p1) / (p0 + m_sqrt(p0 * p0 + ui * (p1 * p1 - p0 * p0)));
   const R xi = (static_cast<R>(bin) + t) * static_cast<R>(1.0 / kNB);
   if (xi_out) *xi_out = xi;
-  return reduced_to_physical<R>(m, E, xi, static_cast<R>(M.cut));
+  return reduced_to_physical<R>(m, E, xi, V.rc.cut[m]);
 }
 
 // ---------------------------------------------------------------- geometry
 // Distance to the boundary of sub-slab `sub`: FP64 coordinate differences,
-// divided in R.  next = -1 when the track leaves the box.
+// divided in R.  next = -1 when the track leaves the box.  The plane is
+// chosen before the subtraction, so a warp whose lanes move both ways still
+// issues one FP64 difference per axis.
 template <typename R>
 __device__ __forceinline__ R distance(const View<R> &V, double x, double y, double z, R u, R v, R w, int sub,
                                       int &next, int &plane) {
   R d = r_inf<R>();
   int nx = sub, pl = -1;
-  if (w > R(0)) {
-    d = static_cast<R>(V.zb[sub + 1] - z) / w;
-    nx = sub + 1;
-    pl = sub + 1;
-  } else if (w < R(0)) {
-    d = static_cast<R>(V.zb[sub] - z) / w;
-    nx = sub - 1;
-    pl = sub;
+  if (w != R(0)) {
+    const int up = w > R(0) ? 1 : 0;
+    pl = sub + up;
+    nx = up ? sub + 1 : sub - 1;
+    d = static_cast<R>(V.zb[pl] - z) / w;
   }
-  if (V.geo.hx > 0.0) {
-    R dx = r_inf<R>();
-    if (u > R(0)) dx = static_cast<R>(V.geo.hx - x) / u;
-    else if (u < R(0)) dx = static_cast<R>(-V.geo.hx - x) / u;
+  if (V.geo.walls_x && u != R(0)) {
+    const R dx = static_cast<R>(V.geo.wx[u > R(0) ? 1 : 0] - x) / u;
     if (dx < d) { d = dx; nx = -1; pl = -2; }
   }
-  if (V.geo.hy > 0.0) {
-    R dy = r_inf<R>();
-    if (v > R(0)) dy = static_cast<R>(V.geo.hy - y) / v;
-    else if (v < R(0)) dy = static_cast<R>(-V.geo.hy - y) / v;
+  if (V.geo.walls_y && v != R(0)) {
+    const R dy = static_cast<R>(V.geo.wy[v > R(0) ? 1 : 0] - y) / v;
     if (dy < d) { d = dy; nx = -1; pl = -3; }
   }
   if (d < R(0)) d = R(0);
@@ -347,9 +354,9 @@ template <typename R>
 __device__ int interact(const View<R> &V, int type, int p, R &E, R d[3], const R *u, Kids<R> &kids, R &local,
                         int &npair, int &nann) {
   const R ME = static_cast<R>(kME);
-  const R ecut_push = static_cast<R>(V.cut.ecut > V.cut.tcut ? V.cut.ecut : V.cut.tcut);
-  const R tcut = static_cast<R>(V.cut.tcut);
-  const R ec = static_cast<R>(V.cut.ecut);
+  const R ecut_push = V.rc.ecut_push;
+  const R tcut = V.rc.tcut;
+  const R ec = V.rc.ecut;
   local = R(0);
   // which model, and is it open at this energy?
   int model;
@@ -361,7 +368,7 @@ __device__ int interact(const View<R> &V, int type, int p, R &E, R d[3], const R
       model = kPair;
     }
   } else if (p == 0) {
-    if (!(E > static_cast<R>(V.cut.gcut))) return -1;
+    if (!(E > V.rc.gcut)) return -1;
     model = kBrem;
   } else if (p == 1) {
     if (!(E > (type == 1 ? R(2) * ec : ec))) return -1;

@@ -70,8 +70,10 @@ __device__ __forceinline__ void deposit(const View<R> &V, const DevState<R> *S, 
   if (S->cell) {
     const GeoConst &g = V.geo;
     const int layer = sub / g.nsub_layer;
-    int ix = static_cast<int>(floor((px + g.hx) / g.pitch_x));
-    int iy = static_cast<int>(floor((py + g.hy) / g.pitch_y));
+    // the offset from the wall in FP64, the cell index in FP32 (a cell
+    // edge moves by ~1e-7 of the box width; no FP64 division)
+    int ix = __float2int_rd(static_cast<float>(px + g.hx) * g.inv_pitch_x);
+    int iy = __float2int_rd(static_cast<float>(py + g.hy) * g.inv_pitch_y);
     ix = ix < 0 ? 0 : (ix >= g.nx ? g.nx - 1 : ix);
     iy = iy < 0 ? 0 : (iy >= g.ny ? g.ny - 1 : iy);
     atomicAdd(&S->cell[(static_cast<size_t>(layer) * g.nx + ix) * g.ny + iy], static_cast<double>(dE));
@@ -133,7 +135,7 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   // a physics-limited step (process choice and alias uniforms)
   uint4 r0 = make_uint4(0u, 0u, 0u, 0u);
   bool have_r0 = false;
-  const R tcut = static_cast<R>(V.cut.tcut);
+  const R tcut = V.rc.tcut;
   if (t.E < tcut) {  // PreStep: tracking cut
     deposit(V, S, t.ev, t.sub, t.x, t.y, t.E, pd);
     if (t.type == 2) {
@@ -174,20 +176,20 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
     if (t.type == 2) count(S, bc, t.ev, GV_C_EP_ESC);
     return 0;
   }
-  // Propagation (FP64 positions)
-  const double sd = static_cast<double>(s);
+  // Propagation: FP64 positions, advanced by displacements s d formed in R
+  // (s and d are R already; in FP64 mode this is one fused multiply-add)
   double mx = 0.0, my = 0.0;  // step midpoint: only cell scoring reads it
   if (S->cell) {
-    mx = t.x + 0.5 * sd * static_cast<double>(t.u);
-    my = t.y + 0.5 * sd * static_cast<double>(t.v);
+    mx = t.x + static_cast<double>(R(0.5) * s * t.u);
+    my = t.y + static_cast<double>(R(0.5) * s * t.v);
   }
-  t.x += sd * static_cast<double>(t.u);
-  t.y += sd * static_cast<double>(t.v);
-  t.z += sd * static_cast<double>(t.w);
+  t.x += static_cast<double>(s * t.u);
+  t.y += static_cast<double>(s * t.v);
+  t.z += static_cast<double>(s * t.w);
   if (lim == 0) {
     if (plane >= 0) t.z = V.zb[plane];
-    else if (plane == -2) t.x = t.u > R(0) ? V.geo.hx : -V.geo.hx;
-    else if (plane == -3) t.y = t.v > R(0) ? V.geo.hy : -V.geo.hy;
+    else if (plane == -2) t.x = V.geo.wx[t.u > R(0) ? 1 : 0];
+    else if (plane == -3) t.y = V.geo.wy[t.v > R(0) ? 1 : 0];
   }
   if (Sig > R(0)) t.nlam = (lim == 1) ? R(0) : t.nlam - s * Sig;
   t.step = k + 1;
@@ -664,7 +666,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_MIN_BLOCKS : 2)
         ++n_iter;
         const uint32_t before = t.step;
         alive = step_track(V, S, t, kids, kstep, &bc, proc, u, lim, pd) != 0;
-        if (!(t.E == t.E) || !(t.z == t.z)) {
+        // NaN energy, or a non-finite z (tested on its exponent bits: an FP64
+        // comparison would take the FP64 pipe)
+        if (!(t.E == t.E) || (__double2hiint(t.z) & 0x7ff00000) == 0x7ff00000) {
           set_status(ctl, GV_ERR_NUMERIC);
           alive = false;
           proc = -1;
@@ -1010,11 +1014,28 @@ template <typename R> View<R> make_view(const Ctx *c) {
   v.geo.ny = c->geo.ny_cells;
   v.geo.hx = c->geo.half_x_cm;
   v.geo.hy = c->geo.half_y_cm;
+  v.geo.wx[0] = -c->geo.half_x_cm;
+  v.geo.wx[1] = c->geo.half_x_cm;
+  v.geo.wy[0] = -c->geo.half_y_cm;
+  v.geo.wy[1] = c->geo.half_y_cm;
+  v.geo.walls_x = c->geo.half_x_cm > 0.0;
+  v.geo.walls_y = c->geo.half_y_cm > 0.0;
   v.geo.pitch_x = c->geo.nx_cells > 0 ? 2.0 * c->geo.half_x_cm / c->geo.nx_cells : 1.0;
   v.geo.pitch_y = c->geo.ny_cells > 0 ? 2.0 * c->geo.half_y_cm / c->geo.ny_cells : 1.0;
+  v.geo.inv_pitch_x = static_cast<float>(1.0 / v.geo.pitch_x);
+  v.geo.inv_pitch_y = static_cast<float>(1.0 / v.geo.pitch_y);
   v.cut.gcut = c->cuts.gamma_cut_MeV;
   v.cut.ecut = c->cuts.e_cut_MeV;
   v.cut.tcut = c->cuts.track_cut_MeV;
+  v.rc.tcut = static_cast<R>(c->cuts.track_cut_MeV);
+  v.rc.gcut = static_cast<R>(c->cuts.gamma_cut_MeV);
+  v.rc.ecut = static_cast<R>(c->cuts.e_cut_MeV);
+  v.rc.ecut_push = static_cast<R>(std::max(c->cuts.e_cut_MeV, c->cuts.track_cut_MeV));
+  for (int m = 0; m < kNModel; ++m) {
+    v.rc.ln_Elo[m] = static_cast<R>(c->meta[m].ln_Elo);
+    v.rc.inv_dl[m] = static_cast<R>(c->meta[m].inv_dl);
+    v.rc.cut[m] = static_cast<R>(c->meta[m].cut);
+  }
   v.cut.mask = c->cuts.process_mask;
   return v;
 }

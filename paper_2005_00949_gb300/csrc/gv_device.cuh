@@ -141,12 +141,17 @@ template <typename R> __device__ __forceinline__ V4<R> lerp4(const V4<R> &a, con
   return o;
 }
 
+template <typename R>
+__device__ __forceinline__ V4<R> lookup_at(const View<R> &V, int mat, int type, int i, R f) {
+  const V4<R> *t = V.xs + (mat * 3 + type) * kGridN;
+  return lerp4(t[i], t[i + 1], f);
+}
+
 template <typename R> __device__ __forceinline__ V4<R> lookup(const View<R> &V, int mat, int type, R E) {
   int i;
   R f;
   grid_pos(V, E, i, f);
-  const V4<R> *t = V.xs + (mat * 3 + type) * kGridN;
-  return lerp4(t[i], t[i + 1], f);
+  return lookup_at(V, mat, type, i, f);
 }
 
 // range is component z (e-) or w (e+)
@@ -158,11 +163,9 @@ template <typename R> __device__ __forceinline__ R range_at(const V4<R> &v, int 
 // exact inverse of the range interpolated linearly in ln E.  While R(E) - s
 // stays in E's own interval the inverse is E exp(-dl s / (R_{i+1} - R_i)),
 // free of the cancellation R(E) - s suffers for short steps in FP32.
-template <typename R> __device__ R eloss(const View<R> &V, int mat, int type, R E, R s) {
+// (i, f) is E's grid position, as grid_pos returns it.
+template <typename R> __device__ R eloss_at(const View<R> &V, int mat, int type, R E, int i, R f, R s) {
   const V4<R> *t = V.xs + (mat * 3 + type) * kGridN;
-  int i;
-  R f;
-  grid_pos(V, E, i, f);
   const R Ri = range_at(t[i], type), Rj = range_at(t[i + 1], type);
   const R dR = Rj - Ri;
   const R Rv = Ri + f * dR;
@@ -180,6 +183,13 @@ template <typename R> __device__ R eloss(const View<R> &V, int mat, int type, R 
   }
   const R Rh = range_at(t[j + 1], type);
   return m_exp(static_cast<R>(-6.907755278982137) + dl * (static_cast<R>(j) + (r - Rl) / (Rh - Rl)));
+}
+
+template <typename R> __device__ __forceinline__ R eloss(const View<R> &V, int mat, int type, R E, R s) {
+  int i;
+  R f;
+  grid_pos(V, E, i, f);
+  return eloss_at(V, mat, type, E, i, f, s);
 }
 
 // ---------------------------------------------------------------- alias sampling

@@ -152,7 +152,10 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
     have_r0 = true;
     t.nlam = -m_log(u24<R>(r0.x));
   }
-  const V4<R> s4 = lookup(V, mat, t.type, t.E);
+  int gi;  // the pre-step energy's grid position serves the lookup and the loss
+  R gf;
+  grid_pos(V, t.E, gi, gf);
+  const V4<R> s4 = lookup_at(V, mat, t.type, gi, gf);
   const R sig0 = s4.x, sig1 = s4.y, sig2 = (t.type == 1) ? R(0) : s4.z;
   const R Sig = sig0 + sig1 + sig2;
   const R INF = r_inf<R>();
@@ -202,7 +205,7 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   const int pre_sub = t.sub;
   // AlongStepAction
   if (charged) {
-    const R Ep = eloss(V, mat, t.type, t.E, s);
+    const R Ep = eloss_at(V, mat, t.type, t.E, gi, gf, s);
     deposit(V, S, t.ev, pre_sub, mx, my, t.E - Ep, pd);
     t.E = Ep;
     if (t.E < tcut) {
@@ -495,13 +498,22 @@ template <typename R> __global__ void prim_emax_kernel(const DevState<R> *S) {
 // Register budget: GV_MIN_BLOCKS resident 256-thread blocks per SM in FP32
 // (measured: with the along-step loop 2 blocks at up to 128 registers beat
 // 3 blocks at 80 registers, which spill ~700 bytes); FP64 keeps 2 blocks.
+// GV_MAX_BLOCK is the largest block the kernels are compiled for.
 #ifndef GV_MIN_BLOCKS
 #define GV_MIN_BLOCKS 2
 #endif
+#ifndef GV_MAX_BLOCK
 #define GV_MAX_BLOCK 256
+#endif
+
+#ifdef GV_MAXNREG
+#define GV_STEP_BOUNDS __maxnreg__(GV_MAXNREG)
+#else
+#define GV_STEP_BOUNDS __launch_bounds__(GV_MAX_BLOCK, sizeof(R) == 4 ? GV_MIN_BLOCKS : 2)
+#endif
 
 template <typename R, bool SORT, bool MERGE>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_MIN_BLOCKS : 2)
+__global__ void GV_STEP_BOUNDS
     step_kernel(const DevState<R> *__restrict__ S, int parity) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ View<R> sV;

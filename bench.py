@@ -17,6 +17,8 @@ on a bounded sample of the same workload on the host cores.
 from __future__ import annotations
 
 import argparse
+import datetime
+import hashlib
 import json
 import math
 import os
@@ -49,6 +51,33 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ["gv_transport.cu", "gv_device.cuh", "gv_state.cuh", "gv_internal.h"]
+
+
+def kernel_source_hash() -> str:
+    """sha1 over the step kernel's sources: a DRAM-traffic figure taken with
+    ncu holds only while it matches."""
+    h = hashlib.sha1()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2005_00949_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _traffic_per_launch():
+    """dram__bytes_read.sum + dram__bytes_write.sum per step-kernel launch of
+    this workload, from the ncu capture summarised in profiles/ (None if the
+    kernel sources changed since)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "step_kernel_dram_traffic.json")) as f:
+            t = json.load(f)
+        if t.get("kernel_source_sha1") != kernel_source_hash():
+            return None
+        return float(t["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def _workload(rank: int):
     wl = W.pbps_electrons(N_EVENTS, E0)
     # each rank owns a distinct event range (distinct Philox streams)
@@ -57,24 +86,32 @@ def _workload(rank: int):
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling (every 100 ms) around the timed region; the summary
+    keeps the samples taken between mark_start() and mark_end()."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device: int):
         self.device = device
         self.p = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
         return self
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def __exit__(self, *a):
         self.rows = []
@@ -85,19 +122,28 @@ class Clocks:
         out, _ = self.p.communicate(timeout=10)
         for line in out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) >= 9:
+            if len(f) >= 10:
+                try:  # local wall-clock time of the sample
+                    f[0] = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    f[0] = None
                 self.rows.append(f)
 
     def summary(self):
-        if not getattr(self, "rows", None):
+        rows = getattr(self, "rows", None) or []
+        if rows and self.t0 is not None and self.t1 is not None:
+            inside = [r for r in rows if r[0] is not None and self.t0 - 0.05 <= r[0] <= self.t1 + 0.05]
+            if inside:
+                rows = inside
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i] == "Active"})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.rows)}
+                "samples": len(rows)}
 
 
 def cpu_baseline(wl, budget_events: int | None = None, repeats: int = 3):
@@ -175,7 +221,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gv")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -231,6 +277,8 @@ def main():
     barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
+        time.sleep(0.3)  # let the sampler start
+        clk.mark_start()
         for i in range(args.steps):
             flush.fill_(i & 0xff)
             starts[i].record(stream)
@@ -241,6 +289,7 @@ def main():
             kernel_ms += res.kernel_ms
             launches += ctx.lib.gv_last_launches(ctx.h)
         torch.cuda.synchronize()
+        clk.mark_end()
     barrier()
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     if dist is not None:
@@ -279,14 +328,7 @@ def main():
     sec_per_step = sec / max(steps_tot, 1)
     alg_bytes = steps_tot / world * (2 * TRACK_BYTES + TRACK_BYTES * sec_per_step)
     achieved = alg_bytes / (kernel_ms / 1000.0) / 1e9 if kernel_ms > 0 else None
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic = json.load(f).get("dram_bytes_per_step_mixed")
-            if traffic is not None:
-                traffic = traffic * steps_tot / args.steps / max(launches / args.steps, 1)
-    except Exception:
-        traffic = None
+    traffic = _traffic_per_launch() if args.events == N_EVENTS else None
     line = {
         "metric": METRIC, "value": value, "unit": "showers/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,

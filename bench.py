@@ -329,6 +329,8 @@ def main():
     alg_bytes = steps_tot / world * (2 * TRACK_BYTES + TRACK_BYTES * sec_per_step)
     achieved = alg_bytes / (kernel_ms / 1000.0) / 1e9 if kernel_ms > 0 else None
     traffic = _traffic_per_launch() if args.events == N_EVENTS else None
+    c = list(res.counters)
+    working_launches = max(c[11], 1)  # generations of the last transport
     line = {
         "metric": METRIC, "value": value, "unit": "showers/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -349,10 +351,11 @@ def main():
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "kernel": "gv::step_kernel<float>",
-                     "alg_bytes_per_step": 2 * TRACK_BYTES + TRACK_BYTES * sec_per_step},
+                     "alg_bytes_per_step": 2 * TRACK_BYTES + TRACK_BYTES * sec_per_step,
+                     "alg_bytes_per_launch": alg_bytes / args.steps / working_launches,
+                     "traffic_unit": "DRAM bytes per working launch (ncu, full-size workload)"},
         "clocks": clk.summary(),
     }
-    c = list(res.counters)
     line["diagnostics"] = {
         "generations": c[11], "live_peak": c[15],
         "geometry_limited_frac": c[12] / max(c[0], 1), "discrete_frac": c[13] / max(c[0], 1),

@@ -1,0 +1,144 @@
+"""The workloads at full size, three ways: GPU FP64, GPU mixed precision and
+the FP64 oracle.
+
+Besides the parity criteria these tests measure what each configuration is
+reported by (steps/s, events/s, idle lanes, peak live tracks, the precision
+study of the 10 GeV workload).  With GV_REPORT=<file> set they append one
+JSON line per measurement to that file.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2005_00949_gb300 import workloads as W
+from test_gpu_transport import ME, NTHR, _T0, _ctx, gvmod, layer_parity  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def _report(name, **kw):
+    path = os.environ.get("GV_REPORT")
+    if not path:
+        return
+    with open(path, "a") as f:
+        f.write(json.dumps({"name": name, **kw}) + "\n")
+
+
+def _run(gvmod, wl, **cfg):
+    ctx = _ctx(gvmod, wl, **cfg)
+    ctx.transport(wl, per_event=cfg.get("per_event_counts", 0) == 1)  # warm-up (graph capture)
+    r = ctx.transport(wl, per_event=cfg.get("per_event_counts", 0) == 1)
+    ctx.close()
+    assert r["status"] == 0
+    return r
+
+
+def _conservation(wl, r):
+    """Per-event relative residual of T + 2m (N_annih - N_pair) = E_dep + E_esc."""
+    c = r["counts"]
+    T0 = _T0(wl)
+    return (r["edep"].sum(1) + r["escape"] - (T0 + 2 * ME * (c[:, 8] - c[:, 7]))) / T0
+
+
+def _layer_stats(wl, g_edep, o_edep):
+    n = wl.n_events
+    g = g_edep.reshape(n, wl.n_layers, -1).sum(2)
+    o = o_edep.reshape(n, wl.n_layers, -1).sum(2)
+    mg, mo = g.mean(0), o.mean(0)
+    comb = np.sqrt(g.var(0, ddof=1) / n + o.var(0, ddof=1) / n)
+    big = mo >= 0.01 * mo.sum()
+    rel = (mg - mo)[big] / mo[big]
+    pull = np.abs(mg - mo)[comb > 0] / comb[comb > 0]
+    return {"layers_compared": int(big.sum()), "max_abs_rel_err": float(np.abs(rel).max()),
+            "rms_rel_err": float(np.sqrt((rel ** 2).mean())), "max_pull": float(pull.max()),
+            "total_rel_err": float(g.sum() / o.sum() - 1.0)}
+
+
+def test_precision_study_10GeV(gvmod, oracle_mod):
+    """2000 x 10 GeV e- on Pb/polystyrene: FP64 GPU, mixed GPU and the oracle."""
+    wl = W.config(4)
+    ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
+    o_res = (ref["edep"].sum(1) + ref["escape"]
+             - (_T0(wl) + 2 * ME * (ref["counts"][:, 8] - ref["counts"][:, 7]))) / _T0(wl)
+    assert np.abs(o_res).max() < 1e-9
+    out = {"oracle_conservation_max": float(np.abs(o_res).max())}
+    for name, prec in (("fp64", 1), ("mixed", 0)):
+        r = _run(gvmod, wl, precision=prec, per_event_counts=1, stack_capacity=1 << 23)
+        layer_parity(wl, r["edep"], ref["edep"])
+        res = _conservation(wl, r)
+        assert np.abs(res).max() < (1e-9 if prec == 1 else 1e-5), np.abs(res).max()
+        same = np.all(r["counts"][:, :11] == ref["counts"][:, :11], axis=1)
+        out[name] = {**_layer_stats(wl, r["edep"], ref["edep"]),
+                     "conservation_max": float(np.abs(res).max()),
+                     "events_identical_counts": float(same.mean()),
+                     "steps": int(r["counts"][:, 0].sum()), "kernel_ms": r["kernel_ms"]}
+    out["oracle_steps"] = int(ref["counts"][:, 0].sum())
+    _report("precision_10GeV_PbPS", **out)
+
+
+def test_config2_1GeV(gvmod, oracle_mod):
+    wl = W.config(2)
+    r = _run(gvmod, wl)
+    ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
+    layer_parity(wl, r["edep"], ref["edep"])
+    c = r["counters"]
+    _report("config2_1GeV_PbPS", events=wl.n_events, kernel_ms=r["kernel_ms"],
+            events_per_s=wl.n_events / (r["kernel_ms"] / 1e3), steps_per_s=c["steps"] / (r["kernel_ms"] / 1e3),
+            layers=_layer_stats(wl, r["edep"], ref["edep"]))
+
+
+def test_config3_mixed_types_measured(gvmod):
+    wl = W.config(3)
+    r = _run(gvmod, wl, stack_capacity=1 << 23)
+    c = r["counters"]
+    T0 = _T0(wl).sum()
+    tot = r["edep"].sum() + r["escape"].sum()
+    assert abs(tot - (T0 + 2 * ME * (c["n_annih"] - c["n_pair"]))) < 1e-6 * T0
+    _report("config3_mixed_types", events=wl.n_events, kernel_ms=r["kernel_ms"],
+            events_per_s=wl.n_events / (r["kernel_ms"] / 1e3), steps_per_s=c["steps"] / (r["kernel_ms"] / 1e3),
+            idle_lane_frac=1.0 - c["steps"] / max(c["lane_slots"], 1), live_peak=c["live_peak"],
+            generations=c["generations"], launches=r["launches"])
+
+
+def test_config5_full_size(gvmod, oracle_mod):
+    """1e4 x 100 GeV e- on W/Si with 32x32 cells: the whole run on the GPU,
+    the oracle on the first 1000 events."""
+    wl = W.config(5)
+    cap = 1 << 23
+    r = _run(gvmod, wl, stack_capacity=cap)
+    c = r["counters"]
+    assert c["live_peak"] <= cap
+    per_layer = r["edep"].reshape(wl.n_events, 50, 2).sum((0, 2))
+    assert np.allclose(r["cell"].sum((1, 2)), per_layer, rtol=1e-9)
+    T0 = _T0(wl).sum()
+    tot = r["edep"].sum() + r["escape"].sum()
+    assert abs(tot - (T0 + 2 * ME * (c["n_annih"] - c["n_pair"]))) < 1e-6 * T0
+    sub = wl.subset(1000)
+    ref = oracle_mod.Oracle(sub).transport(n_threads=NTHR)
+    layer_parity(sub, r["edep"][:1000], ref["edep"])
+    _report("config5_WSi_cells_100GeV", events=wl.n_events, kernel_ms=r["kernel_ms"],
+            events_per_s=wl.n_events / (r["kernel_ms"] / 1e3), steps_per_s=c["steps"] / (r["kernel_ms"] / 1e3),
+            steps=c["steps"], live_peak=c["live_peak"], capacity=cap, generations=c["generations"],
+            layers_first1000=_layer_stats(sub, r["edep"][:1000], ref["edep"]))
+
+
+def test_testem3_pb_lar(gvmod, oracle_mod):
+    """The paper's TestEm3 layout (50 x (2.3 mm Pb + 5.7 mm LAr)), 10 GeV e-,
+    without its field and multiple scattering: parity with the oracle, and the
+    per-material deposits and secondary counts next to the paper's table
+    (context only: different physics list and cuts)."""
+    wl = W.pblar_testem3(1000, 10_000.0)
+    r = _run(gvmod, wl, per_event_counts=1)
+    ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
+    layer_parity(wl, r["edep"], ref["edep"])
+    res = _conservation(wl, r)
+    assert np.abs(res).max() < 1e-5
+    mat = r["edep"].reshape(wl.n_events, 50, 2).sum(1).mean(0)
+    cnt = r["counts"].mean(0)
+    _report("testem3_PbLAr_10GeV", events=wl.n_events, kernel_ms=r["kernel_ms"],
+            edep_Pb_GeV=float(mat[0] / 1e3), edep_LAr_GeV=float(mat[1] / 1e3),
+            gammas=float(cnt[4]), electrons=float(cnt[5] - 1), positrons=float(cnt[6]),
+            charged_steps=float(cnt[2] + cnt[3]), neutral_steps=float(cnt[1]),
+            layers=_layer_stats(wl, r["edep"], ref["edep"]))

@@ -10,6 +10,9 @@ time (median of repeats).  Knobs:
   refill_low_water, refill_batch -- event-server refill thresholds (live-track
                                     budget below which primaries are injected)
   process_sort                   -- in-block re-basketing by selected process
+  claim_chunks                   -- per-block or per-warp work claims
+  along_steps                    -- steps a lane takes before its block baskets
+  scoring                        -- direct or warp-merged tally atomics
 Integer results do not depend on any of these (per-track random streams), so
 the tuner only trades time.
 """
@@ -24,10 +27,12 @@ from . import gv, workloads as W
 SPACE = {
     "process_sort": [1, 0],
     "claim_chunks": [0, 1],
+    "along_steps": [2, 3, 4, 6],
+    "scoring": [0, 1],
     "block_size": [128, 256],
     "blocks_per_sm": [2, 3, 4],
     "steps_per_claim": [1, 2, 3, 4],
-    "tail_steps_per_claim": [4, 8, 16, 32],
+    "tail_steps_per_claim": [1, 2, 4, 8, 16],
     "tail_threshold": [1 << 15, 1 << 17, 1 << 19],
     "refill_low_water": [1 << 19, 1 << 21, 1 << 23],
     "refill_batch": [1 << 8, 1 << 11, 1 << 14],

@@ -1310,7 +1310,7 @@ int gv_default_config(gv_config *cfg) {
   cfg->block_size = 256;
   cfg->blocks_per_sm = 2;
   cfg->steps_per_claim = 1;
-  cfg->tail_steps_per_claim = 8;
+  cfg->tail_steps_per_claim = 4;
   cfg->tail_threshold = 100000;
   cfg->stack_capacity = 1ll << 23;
   cfg->refill_low_water = 1ll << 21;

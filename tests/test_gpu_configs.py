@@ -142,3 +142,16 @@ def test_testem3_pb_lar(gvmod, oracle_mod):
             gammas=float(cnt[4]), electrons=float(cnt[5] - 1), positrons=float(cnt[6]),
             charged_steps=float(cnt[2] + cnt[3]), neutral_steps=float(cnt[1]),
             layers=_layer_stats(wl, r["edep"], ref["edep"]))
+
+
+def test_autotuner_keeps_results(gvmod):
+    """The tuner only trades time: its pick runs, and integer results do not
+    depend on the knobs it turns."""
+    from paper_2005_00949_gb300 import autotune
+    wl = W.pbps_electrons(60, 2000.0)
+    space = {"along_steps": [2, 4], "block_size": [128, 256], "scoring": [0, 1]}
+    knobs, ms = autotune.tune(wl, passes=1, repeats=1, space=space, budget_s=60.0)
+    assert set(knobs) == set(space) and ms > 0
+    base = _run(gvmod, wl, per_event_counts=1)
+    tuned = _run(gvmod, wl, per_event_counts=1, **knobs)
+    assert np.array_equal(base["counts"][:, :11], tuned["counts"][:, :11])

@@ -241,6 +241,20 @@ def test_failure_statuses_are_reported_without_hanging(gvmod):
     # the contexts stay usable after an error
     small = W.pbps_electrons(2, 100.0)
     assert ctx.transport(small)["status"] == 0
+    # records on the device are checked by the kernel: a bad type is refused,
+    # a NaN energy ends as a numeric error (every index stays clamped)
+    import torch
+    for field, value, code in (("type", 7, -1), ("E", float("nan"), -6)):
+        p = W.make_primaries(2)
+        p["type"], p["E"], p["w"], p["event"] = 1, 100.0, 1.0, [0, 1]
+        p[field][1] = value
+        prim = torch.from_numpy(p.view(np.uint8).copy()).cuda()
+        edep = torch.zeros((2, ctx.n_subtotal), dtype=torch.float64, device="cuda")
+        esc = torch.zeros(2, dtype=torch.float64, device="cuda")
+        with pytest.raises(gvmod.GvError):
+            ctx.gv_transport(prim, 2, 1, edep, None, esc)
+        assert ctx.last_result.status == code, (field, ctx.last_result.status)
+    assert ctx.transport(small)["status"] == 0
 
 
 def test_host_buffers_give_device_results(gvmod):

@@ -64,3 +64,37 @@ def test_sharded_transport_equals_single_process(oracle_mod):
     assert np.array_equal(full["escape"], ref["escape"])
     assert np.array_equal(full["counts"], ref["counts"])
     assert np.allclose(full["cell"], ref["cell"], rtol=1e-12, atol=1e-12)
+
+
+def _failing_rank_main(rank, world, port, q):
+    """Rank 1 fails between steps (before the gather, nothing in flight);
+    rank 0 must learn of it from its collective instead of waiting forever."""
+    import datetime
+
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=20))
+    if rank == 1:
+        os._exit(3)  # the rank dies without joining the gather
+    local = {"edep": np.zeros((4, 2)), "escape": np.zeros(4)}
+    try:
+        sharding.gather_tallies(dist, local, 0, 2)
+        q.put("gathered")
+    except Exception as e:  # noqa: BLE001 -- any collective error is the detection
+        q.put(f"detected: {type(e).__name__}")
+
+
+def test_a_failed_rank_is_detected_by_the_gather():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    msg = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert msg.startswith("detected"), msg
+    assert procs[1].exitcode == 3

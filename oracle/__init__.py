@@ -98,6 +98,11 @@ def _load():
             lib.or_distance.restype = d
             lib.or_distance.argtypes = [p, p, p, i, C.POINTER(i), C.POINTER(i)]
             lib.or_interact.argtypes = [p, i, i, d, p, p, p]
+            lib.or_safety.restype = d
+            lib.or_safety.argtypes = [p, p, i]
+            lib.or_msc_theta0.restype = d
+            lib.or_msc_theta0.argtypes = [p, i, d, d]
+            lib.or_msc.argtypes = [p, i, d, d, d, p, p, p, p, p]
             lib.or_transport.argtypes = [p, p, C.c_long, C.c_long, C.c_uint64, p, p, p, p, i]
             _lib = lib
     return _lib
@@ -252,6 +257,23 @@ class Oracle:
         nx, pl = C.c_int(), C.c_int()
         s = self.lib.or_distance(self.h, _ptr(p), _ptr(q), sub, C.byref(nx), C.byref(pl))
         return s, nx.value, pl.value
+
+    def safety(self, pos, sub: int) -> float:
+        p = np.ascontiguousarray(pos, dtype=np.float64)
+        return self.lib.or_safety(self.h, _ptr(p), sub)
+
+    # -- multiple scattering
+    def msc_theta0(self, mat: int, T: float, s: float) -> float:
+        return self.lib.or_msc_theta0(self.h, mat, T, s)
+
+    def msc(self, sub: int, E_pre: float, E_post: float, s: float, d, pos, u):
+        """(new direction, new position) after Gaussian scattering over a step."""
+        dd = np.ascontiguousarray(d, dtype=np.float64)
+        pp = np.ascontiguousarray(pos, dtype=np.float64)
+        uu = np.ascontiguousarray(u, dtype=np.float64)
+        od, op = np.zeros(3), np.zeros(3)
+        self.lib.or_msc(self.h, sub, E_pre, E_post, s, _ptr(dd), _ptr(pp), _ptr(uu), _ptr(od), _ptr(op))
+        return od, op
 
     # -- transport
     def transport(self, primaries=None, n_events=None, seed=None, n_threads: int = 1,

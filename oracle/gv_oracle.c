@@ -688,6 +688,83 @@ double or_distance(const or_ctx *c, const double pos[3], const double dir[3], in
   return d;
 }
 
+/* Distance from pos to the nearest boundary of sub-slab `sub` (its two
+ * z-planes and the bounded x/y walls): the isotropic safety of Sec. 3.2. */
+double or_safety(const or_ctx *c, const double pos[3], int sub) {
+  double d = fmin(pos[2] - c->zb[sub], c->zb[sub + 1] - pos[2]);
+  if (c->s.half_x > 0.0) d = fmin(d, c->s.half_x - fabs(pos[0]));
+  if (c->s.half_y > 0.0) d = fmin(d, c->s.half_y - fabs(pos[1]));
+  return d > 0.0 ? d : 0.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* multiple Coulomb scattering (the MSC stages of Sec. 2.1.2)          */
+/* ------------------------------------------------------------------ */
+/* Highland width of the projected angle for a unit-charge track of kinetic
+ * energy T after a path s in material mat:
+ *   theta0 = 13.6 MeV / (beta p c) sqrt(s/X0) (1 + 0.038 ln(s / (X0 beta^2)))
+ * with the bracket floored at 0 (PDG, "Passage of particles through
+ * matter", multiple scattering section).  Parity unpinned beyond special
+ * cases: the paper prints no scattering numbers. */
+double or_msc_theta0(const or_ctx *c, int mat, double T, double s) {
+  if (!(s > 0.0) || !(T > 0.0)) return 0.0;
+  const double pc = sqrt(T * (T + 2.0 * ME));
+  const double beta = pc / (T + ME);
+  const double X0 = c->mat[mat].X0g / c->mat[mat].m.rho;
+  const double x = s / X0;
+  const double corr = 1.0 + 0.038 * log(x / (beta * beta));
+  return corr > 0.0 ? 13.6 / (beta * pc) * sqrt(x) * corr : 0.0;
+}
+
+/* Gaussian multiple scattering over a step of length s that took the
+ * kinetic energy from E_pre to E_post, evaluated at their mean.  Four
+ * uniforms give four standard normals (Box-Muller: radius from the first of
+ * each pair, angle from the second); per transverse plane the angle is
+ * z2 theta0 and the offset s theta0 (z1 / sqrt(12) + z2 / 2), the joint
+ * Gaussian of the PDG section quoted above (correlation sqrt(3)/2).  The two
+ * planes are those of the frame in which rotations act (rotate()): e1, e2
+ * perpendicular to dir.  The new direction has polar angle
+ * theta = |(theta_x, theta_y)| (at most pi) about dir, azimuth along
+ * (theta_x, theta_y).  The offset moves the end point within the sub-slab:
+ * it is shortened to 0.99 of the safety when it is longer. */
+int or_msc(const or_ctx *c, int sub, double E_pre, double E_post, double s, const double dir[3],
+           const double pos[3], const double u[4], double out_dir[3], double out_pos[3]) {
+  const int mat = c->smat[sub];
+  const double th0 = or_msc_theta0(c, mat, 0.5 * (E_pre + E_post), s);
+  const double r1 = sqrt(-2.0 * log(u[0])), r2 = sqrt(-2.0 * log(u[2]));
+  const double z1 = r1 * cos(2.0 * PI * u[1]), z2 = r1 * sin(2.0 * PI * u[1]);
+  const double z3 = r2 * cos(2.0 * PI * u[3]), z4 = r2 * sin(2.0 * PI * u[3]);
+  const double tx = th0 * z1, ty = th0 * z2;
+  const double ox = s * th0 * (z3 / sqrt(12.0) + z1 / 2.0);
+  const double oy = s * th0 * (z4 / sqrt(12.0) + z2 / 2.0);
+  /* frame: e1, e2 perpendicular to dir, as in rotate() */
+  double e1[3], e2[3];
+  const double up = sqrt(dir[0] * dir[0] + dir[1] * dir[1]);
+  if (up > 0.0) {
+    e1[0] = dir[0] * dir[2] / up; e1[1] = dir[1] * dir[2] / up; e1[2] = -up;
+    e2[0] = -dir[1] / up; e2[1] = dir[0] / up; e2[2] = 0.0;
+  } else {
+    e1[0] = dir[2] < 0.0 ? -1.0 : 1.0; e1[1] = 0.0; e1[2] = 0.0;
+    e2[0] = 0.0; e2[1] = 1.0; e2[2] = 0.0;
+  }
+  double th = sqrt(tx * tx + ty * ty);
+  if (th > 0.0) {
+    const double cp = tx / th, sp = ty / th;
+    if (th > PI) th = PI;
+    const double ct = cos(th), st = sin(th);
+    for (int j = 0; j < 3; ++j) out_dir[j] = st * (cp * e1[j] + sp * e2[j]) + ct * dir[j];
+  } else {
+    for (int j = 0; j < 3; ++j) out_dir[j] = dir[j];
+  }
+  double off[3];
+  for (int j = 0; j < 3; ++j) off[j] = ox * e1[j] + oy * e2[j];
+  const double len = sqrt(ox * ox + oy * oy);
+  const double safe = or_safety(c, pos, sub);
+  const double scale = (len > 0.99 * safe) ? (len > 0.0 ? 0.99 * safe / len : 0.0) : 1.0;
+  for (int j = 0; j < 3; ++j) out_pos[j] = pos[j] + scale * off[j];
+  return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* setup                                                               */
 /* ------------------------------------------------------------------ */
@@ -1065,6 +1142,7 @@ static void run_event(const job_t *J, long ev, ostack *st) {
       cnt[OR_C_STEPS] += 1;
       cnt[OR_C_STEPS_G + t.type] += 1;
       int pre_sub = t.sub;
+      const double E_pre = t.E;
       /* AlongStepAction: continuous loss */
       if (charged) {
         double Ep = or_eloss(c, t.type, mat, t.E, sstep);
@@ -1096,6 +1174,17 @@ static void run_event(const job_t *J, long ev, ostack *st) {
           }
           break;
         }
+      }
+      /* AlongStepAction: multiple scattering of a charged track that stays in
+       * the box (counter block 2 of the step) */
+      if (charged && (s->process_mask & OR_P_MSC) && !(lim == 0 && next < 0)) {
+        uint32_t r2[4];
+        double um[4], nd[3], npos[3];
+        ctr[3] = 2u;
+        or_philox4x32_10(ctr, key, r2);
+        for (int j = 0; j < 4; ++j) um[j] = u24(r2[j]);
+        or_msc(c, pre_sub, E_pre, t.E, sstep, t.dir, t.pos, um, nd, npos);
+        for (int j = 0; j < 3; ++j) { t.dir[j] = nd[j]; t.pos[j] = npos[j]; }
       }
       if (lim == 0) {
         if (next < 0) {

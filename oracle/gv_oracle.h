@@ -18,6 +18,8 @@
  *   ionisation       Moller (e-) / Bhabha (e+), discrete above the e- cut;
  *                    restricted Berger-Seltzer (ICRU 37) collision loss below
  *   annihilation     Heitler two-photon, in flight and at rest
+ *   multiple scatt.  optional (OR_P_MSC): Gaussian angle of Highland width
+ *                    and correlated lateral offset, within the safety
  * The stepping loop follows the stage sequence of Sec. 2.1.2 (Fig. "simulation
  * stages"): PreStep, ComputeIntLen, GeomQuery, Propagation, AlongStepAction,
  * PostStepActions, SteppingActions; secondaries go to a LIFO stack (the
@@ -44,7 +46,8 @@ enum { OR_GAMMA = 0, OR_ELECTRON = 1, OR_POSITRON = 2 };
 /* process bits (process_mask) */
 enum {
   OR_P_COMPTON = 1u << 0, OR_P_PHOTO = 1u << 1, OR_P_PAIR = 1u << 2,
-  OR_P_BREM = 1u << 3, OR_P_IONI = 1u << 4, OR_P_ANNIH = 1u << 5
+  OR_P_BREM = 1u << 3, OR_P_IONI = 1u << 4, OR_P_ANNIH = 1u << 5,
+  OR_P_MSC = 1u << 6  /* Gaussian multiple scattering of e+- (along the step) */
 };
 
 /* alias-sampled final-state models */
@@ -122,6 +125,12 @@ double or_plane_z(const or_ctx *c, int k);
 int or_locate(const or_ctx *c, double z, double w);
 double or_distance(const or_ctx *c, const double pos[3], const double dir[3], int sub,
                    int *next_sub, int *plane);
+double or_safety(const or_ctx *c, const double pos[3], int sub);
+
+/* --- multiple scattering (Highland width, Gaussian angle and offset) -- */
+double or_msc_theta0(const or_ctx *c, int mat, double T, double s);
+int or_msc(const or_ctx *c, int sub, double E_pre, double E_post, double s, const double dir[3],
+           const double pos[3], const double u[4], double out_dir[3], double out_pos[3]);
 
 /* --- interactions given uniforms (unit level) ------------------------ */
 int or_interact(const or_ctx *c, int type, int proc, double E, const double dir[3],

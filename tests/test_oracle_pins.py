@@ -495,3 +495,89 @@ def test_shower_profile_sanity(oracle_mod):
     per_layer = r["edep"].reshape(40, 50, 2).sum(2).mean(0)
     assert per_layer.sum() / 10_000.0 > 0.95
     assert 12 <= int(np.argmax(per_layer)) <= 24
+
+
+# ---------------------------------------------------------------- multiple scattering
+# Pins of the Gaussian scattering step against the closed forms of the
+# joint angle/offset Gaussian (PDG): per transverse plane var(theta) = th0^2,
+# var(offset) = s^2 th0^2 / 3, correlation sqrt(3)/2; space angle Rayleigh,
+# P(theta > t) = exp(-t^2 / (2 th0^2)); deflection symmetric about the
+# incoming direction.  The Highland width itself is a builder's formula.
+def _msc_samples(o, n, d, pos, sub, E=1000.0, s=0.1, seed=11):
+    rng = np.random.default_rng(seed)
+    u = 1.0 - rng.random((n, 4))  # (0, 1]
+    dirs = np.empty((n, 3))
+    offs = np.empty((n, 3))
+    for i in range(n):
+        nd, npos = o.msc(sub, E, E, s, d, pos, u[i])
+        dirs[i] = nd
+        offs[i] = npos - np.asarray(pos)
+    return dirs, offs
+
+
+def _perp_basis(d, rng):
+    d = np.asarray(d, float) / np.linalg.norm(d)
+    a = rng.normal(size=3)
+    a -= a.dot(d) * d
+    a /= np.linalg.norm(a)
+    return a, np.cross(d, a)
+
+
+@pytest.mark.parametrize("d", [(0.0, 0.0, 1.0), (0.3, -0.4, math.sqrt(0.75)), (0.0, 0.0, -1.0)])
+def test_msc_angle_and_offset_moments(oracle_mod, d):
+    o = oracle_mod.Oracle(W.pbps_electrons(1))
+    E, s, n = 1000.0, 0.1, 100_000
+    th0 = o.msc_theta0(0, E, s)
+    assert 1e-3 < th0 < 1e-2
+    pos = (0.0, 0.0, 0.1)  # middle of the first Pb sub-slab (0 .. 0.2 cm): safety 0.1
+    dirs, offs = _msc_samples(o, n, d, pos, 0, E, s)
+    assert np.abs(np.linalg.norm(dirs, axis=1) - 1.0).max() < 1e-12
+    a, b = _perp_basis(d, np.random.default_rng(5))
+    dd = np.asarray(d) / np.linalg.norm(d)
+    ta = dirs @ a / (dirs @ dd)  # projected angles (tan, th0 ~ 5e-3)
+    tb = dirs @ b / (dirs @ dd)
+    se = th0 ** 2 * math.sqrt(2.0 / n)
+    for t in (ta, tb):
+        assert abs(t.var() - th0 ** 2) < 4 * se + 1e-4 * th0 ** 2
+        assert abs(t.mean()) < 4 * th0 / math.sqrt(n)
+    assert abs(np.mean(ta * tb)) < 4 * se  # independent planes
+    # lateral offsets perpendicular to the incoming direction, variance s^2 th0^2 / 3
+    assert np.abs(offs @ dd).max() < 1e-15
+    oa, ob = offs @ a, offs @ b
+    v = (s * th0) ** 2 / 3.0
+    assert np.abs(offs).max() < 0.099  # inside the safety
+    for off_p, t in ((oa, ta), (ob, tb)):
+        assert abs(off_p.var() / v - 1.0) < 4 * math.sqrt(2.0 / n)
+        rho = np.corrcoef(off_p, t)[0, 1]
+        assert abs(rho - math.sqrt(3.0) / 2.0) < 0.01
+    # space angle: Rayleigh tail
+    th = np.arccos(np.clip(dirs @ dd, -1, 1))
+    for k in (1.0, 2.0):
+        p = math.exp(-k * k / 2.0)
+        assert abs((th > k * th0).mean() - p) < 4 * math.sqrt(p * (1 - p) / n)
+
+
+def test_msc_special_cases_and_safety(oracle_mod):
+    wl = W.pbps_electrons(1)
+    o = oracle_mod.Oracle(wl)
+    d = np.array([0.0, 0.6, 0.8])
+    u = [0.3, 0.2, 0.7, 0.9]
+    # zero step: nothing changes
+    nd, npos = o.msc(0, 100.0, 100.0, 0.0, d, [1.0, 2.0, 0.1], u)
+    assert np.array_equal(nd, d) and np.array_equal(npos, [1.0, 2.0, 0.1])
+    assert o.msc_theta0(0, 100.0, 0.0) == 0.0
+    # ultra-relativistic: the width falls as 1/p
+    assert abs(o.msc_theta0(0, 1e6, 0.1) / o.msc_theta0(0, 2e6, 0.1) - 2.0) < 1e-6
+    # the offset never leaves the sub-slab, whatever the width
+    rng = np.random.default_rng(3)
+    zb = [o.plane_z(k) for k in range(3)]
+    for _ in range(3000):
+        sub = int(rng.integers(0, 2))
+        z = zb[sub] + (zb[sub + 1] - zb[sub]) * rng.random()
+        pos = np.array([rng.uniform(-20, 20), rng.uniform(-20, 20), z])
+        dirn = rng.normal(size=3)
+        dirn /= np.linalg.norm(dirn)
+        _, npos = o.msc(sub, 2.0, 1.5, 0.05, dirn, pos, 1.0 - rng.random(4))
+        assert zb[sub] <= npos[2] <= zb[sub + 1]
+        assert abs(npos[0]) <= 20.0 and abs(npos[1]) <= 20.0
+        assert np.linalg.norm(npos - pos) <= 0.99 * o.safety(pos, sub) + 1e-12  # pos ~ 20: ulp 4e-15

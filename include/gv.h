@@ -46,6 +46,7 @@ extern "C" {
 #define GV_P_BREM (1u << 3)
 #define GV_P_IONI (1u << 4)
 #define GV_P_ANNIH (1u << 5)
+#define GV_P_MSC (1u << 6)   /* Gaussian multiple scattering of e+- along the step (off by default) */
 
 /* arithmetic of the stepping loop */
 #define GV_MIXED 0 /* FP32 physics, tables and energies; FP64 positions and boundaries */
@@ -92,7 +93,8 @@ typedef struct {
 /* Production cuts (MeV): gamma_cut splits bremsstrahlung into continuous and
  * discrete parts, e_cut splits ionisation and decides whether Compton,
  * photo- and pair-produced leptons are tracked; track_cut (>= 1 keV) ends
- * tracks.  process_mask: GV_P_* bits of the enabled discrete processes. */
+ * tracks.  process_mask: GV_P_* bits of the enabled discrete processes, plus
+ * GV_P_MSC for multiple scattering along charged steps. */
 typedef struct {
   double gamma_cut_MeV, e_cut_MeV, track_cut_MeV;
   unsigned process_mask;
@@ -257,6 +259,17 @@ int gv_unit_interact(void *ctx, int type, int proc, const double *E, const doubl
  * of Sec. 3.2) from pos[3i..] along dir[3i..]; next[i] = sub-slab entered
  * (-1 = leaves the box), plane[i] = crossed z-plane index or -2/-3 for the
  * x/y walls. */
+/* Multiple scattering over one charged step (the along-step part of GV_P_MSC,
+ * independent of the context's process mask): for each i, a track of
+ * kinetic energy E_pre[i] that ends the step of length s[i] cm in sub-slab
+ * sub[i] with energy E_post[i], direction dir[3i..3i+2] and position
+ * pos[3i..3i+2], scattered with the uniforms u[4i..4i+3] (in (0,1]).
+ * Writes the new direction to out_dir[3i..] and the new position to
+ * out_pos[3i..].  Device arrays; sub[i] outside the geometry gives NaN. */
+int gv_unit_msc(void *ctx, const int *sub, const double *E_pre, const double *E_post, const double *s,
+                const double *dir, const double *pos, const double *u, long long n, double *out_dir,
+                double *out_pos, void *stream);
+
 int gv_unit_distance(void *ctx, const double *pos, const double *dir, const int *sub,
                      long long n, double *dist, int *next, int *plane, void *stream);
 

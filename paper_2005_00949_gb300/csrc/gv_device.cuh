@@ -61,6 +61,7 @@ struct CutConst {
 template <typename R> struct RConst {
   R tcut, gcut, ecut, ecut_push;  // ecut_push = max(e- cut, tracking cut)
   R ln_Elo[kNModel], inv_dl[kNModel], cut[kNModel];
+  R inv_X0[GV_MAX_MAT];  // 1 / radiation length, 1/cm
 };
 
 // Read-only view of everything one step needs.
@@ -340,6 +341,81 @@ __device__ __forceinline__ void rotate_vec(const R d[3], R along, R perp, R cp, 
   }
   const R inv = R(1) / m_sqrt(n2);
   rotate(d, along * inv, perp * inv, cp, sp, o);
+}
+
+// ---------------------------------------------------------------- multiple scattering
+// Gaussian multiple scattering over a charged step of length s (the MSC
+// stages of Sec. 2.1.2; optional process GV_P_MSC).  Width: the Highland
+// formula at the step's mean kinetic energy, with its bracket floored at 0,
+//   th0 = 13.6 MeV / (beta p c) sqrt(s/X0) (1 + 0.038 ln(s / (X0 beta^2))).
+// Four uniforms give four normals by Box-Muller; per transverse plane of the
+// rotation frame the angle is th0 z_a and the lateral offset
+// s th0 (z_b / sqrt(12) + z_a / 2), the correlated joint Gaussian of the
+// small-angle theory.  The direction turns by |(theta_x, theta_y)| (at most
+// pi) towards (theta_x, theta_y); the end point moves by the offset,
+// shortened to 0.99 of the safety (distance to the nearest boundary of
+// sub-slab `sub`, from FP64 differences) when longer.
+template <typename R>
+__device__ __forceinline__ void msc_step(const View<R> &V, int sub, R E_pre, R E_post, R s, R d[3], double &x,
+                                         double &y, double &z, const R u[4]) {
+  const R ME = static_cast<R>(kME);
+  const R T = R(0.5) * (E_pre + E_post);
+  const R pc = m_sqrt(T * (T + R(2) * ME));
+  const R beta = pc / (T + ME);
+  const R xr = s * V.rc.inv_X0[V.smat[sub]];
+  const R corr = R(1) + R(0.038) * m_log(xr / (beta * beta));
+  const R th0 = corr > R(0) ? R(13.6) / (beta * pc) * m_sqrt(xr) * corr : R(0);
+  if (!(th0 > R(0))) return;
+  const R r1 = m_sqrt(R(-2) * m_log(u[0])), r2 = m_sqrt(R(-2) * m_log(u[2]));
+  R s1, c1, s2, c2;
+  m_sincos(static_cast<R>(2.0 * kPi) * u[1], &s1, &c1);
+  m_sincos(static_cast<R>(2.0 * kPi) * u[3], &s2, &c2);
+  const R z1 = r1 * c1, z2 = r1 * s1, z3 = r2 * c2, z4 = r2 * s2;
+  const R tx = th0 * z1, ty = th0 * z2;
+  const R k12 = static_cast<R>(0.28867513459481287);  // 1/sqrt(12)
+  const R ox = s * th0 * (z3 * k12 + z1 * R(0.5));
+  const R oy = s * th0 * (z4 * k12 + z2 * R(0.5));
+  // the frame of rotate(): e1, e2 perpendicular to d
+  R e1[3], e2[3];
+  const R up = m_sqrt(d[0] * d[0] + d[1] * d[1]);
+  if (up > R(0)) {
+    e1[0] = d[0] * d[2] / up; e1[1] = d[1] * d[2] / up; e1[2] = -up;
+    e2[0] = -d[1] / up; e2[1] = d[0] / up; e2[2] = R(0);
+  } else {
+    e1[0] = d[2] < R(0) ? R(-1) : R(1); e1[1] = R(0); e1[2] = R(0);
+    e2[0] = R(0); e2[1] = R(1); e2[2] = R(0);
+  }
+  // offset, limited by the safety of the pre-move end point
+  const R len = m_sqrt(ox * ox + oy * oy);
+  double sf = z - V.zb[sub];
+  const double sz2 = V.zb[sub + 1] - z;
+  sf = sz2 < sf ? sz2 : sf;
+  if (V.geo.walls_x) {
+    const double sx = V.geo.hx - fabs(x);
+    sf = sx < sf ? sx : sf;
+  }
+  if (V.geo.walls_y) {
+    const double sy = V.geo.hy - fabs(y);
+    sf = sy < sf ? sy : sf;
+  }
+  const R safe = sf > 0.0 ? static_cast<R>(sf) : R(0);
+  const R scale = (len > R(0.99) * safe) ? (len > R(0) ? R(0.99) * safe / len : R(0)) : R(1);
+  x += static_cast<double>(scale * (ox * e1[0] + oy * e2[0]));
+  y += static_cast<double>(scale * (ox * e1[1] + oy * e2[1]));
+  z += static_cast<double>(scale * (ox * e1[2] + oy * e2[2]));
+  // direction
+  R th = m_sqrt(tx * tx + ty * ty);
+  if (!(th > R(0))) return;
+  const R cp = tx / th, sp = ty / th;
+  const R PI = static_cast<R>(kPi);
+  th = th > PI ? PI : th;
+  R st, ct;
+  m_sincos(th, &st, &ct);
+  const R dn[3] = {st * (cp * e1[0] + sp * e2[0]) + ct * d[0], st * (cp * e1[1] + sp * e2[1]) + ct * d[1],
+                   st * (cp * e1[2] + sp * e2[2]) + ct * d[2]};
+  d[0] = dn[0];
+  d[1] = dn[1];
+  d[2] = dn[2];
 }
 
 template <typename R> __device__ __forceinline__ void at_rest(Kids<R> &k, R u6, R u7) {

@@ -43,6 +43,7 @@ struct HostTables {
   std::vector<double> a_pdf[kNModel];  // [nE][kNB+1]
   std::vector<float> a_q[kNModel];     // [nE][kNB]
   std::vector<int> a_alias[kNModel];   // [nE][kNB]
+  double inv_X0_cm[GV_MAX_MAT] = {0, 0, 0, 0};  // 1 / radiation length per material, 1/cm
 };
 
 int build_host_tables(const gv_material *mats, int n_mats, const gv_cuts &cuts, HostTables *out,

@@ -324,6 +324,7 @@ int build_host_tables(const gv_material *mats, int n_mats, const gv_cuts &cuts, 
   const unsigned pm = cuts.process_mask;
   for (int m = 0; m < n_mats; ++m) {
     const Medium md = make_medium(mats[m]);
+    out->inv_X0_cm[m] = md.inv_X0_cm;
     auto at = [&](int type, int i, int q) -> double & {
       return out->xs[((static_cast<size_t>(m) * 3 + type) * kGridN + i) * 4 + q];
     };

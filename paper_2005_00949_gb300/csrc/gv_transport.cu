@@ -203,6 +203,7 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
     atomicAdd(&S->evcnt[static_cast<size_t>(t.ev) * GV_NCOUNT + GV_C_STEPS_G + t.type], 1ull);
   }
   const int pre_sub = t.sub;
+  const R E_pre = t.E;
   // AlongStepAction
   if (charged) {
     const R Ep = eloss_at(V, mat, t.type, t.E, gi, gf, s);
@@ -216,6 +217,16 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
         count(S, bc, t.ev, GV_C_ANNIH);
       }
       return 0;
+    }
+    // multiple scattering of a track that stays in the box (counter block 2)
+    if ((V.cut.mask & GV_P_MSC) && !(lim == 0 && next < 0)) {
+      const uint4 r2 = philox4x32_10(make_uint4(idlo, idhi, k, 2u), key0, key1);
+      const R um[4] = {u24<R>(r2.x), u24<R>(r2.y), u24<R>(r2.z), u24<R>(r2.w)};
+      R dm[3] = {t.u, t.v, t.w};
+      msc_step(V, pre_sub, E_pre, t.E, s, dm, t.x, t.y, t.z, um);
+      t.u = dm[0];
+      t.v = dm[1];
+      t.w = dm[2];
     }
   }
   if (lim == 0) {
@@ -1048,6 +1059,7 @@ template <typename R> View<R> make_view(const Ctx *c) {
     v.rc.inv_dl[m] = static_cast<R>(c->meta[m].inv_dl);
     v.rc.cut[m] = static_cast<R>(c->meta[m].cut);
   }
+  for (int m = 0; m < GV_MAX_MAT; ++m) v.rc.inv_X0[m] = static_cast<R>(c->ht.inv_X0_cm[m]);
   v.cut.mask = c->cuts.process_mask;
   return v;
 }

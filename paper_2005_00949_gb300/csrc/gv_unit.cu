@@ -107,6 +107,29 @@ __global__ void k_distance(View<R> V, const double *pos, const double *dir, cons
   plane[i] = pl;
 }
 
+template <typename R>
+__global__ void k_msc(View<R> V, const int *sub, const double *Ea, const double *Eb, const double *sv,
+                      const double *dir, const double *pos, const double *u, long long n, double *od, double *op) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  if (sub[i] < 0 || sub[i] >= V.geo.nsub) {  // not a sub-slab: report, touch no table
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    for (int j = 0; j < 3; ++j) od[3 * i + j] = op[3 * i + j] = nan;
+    return;
+  }
+  R d[3] = {static_cast<R>(dir[3 * i]), static_cast<R>(dir[3 * i + 1]), static_cast<R>(dir[3 * i + 2])};
+  const R uu[4] = {static_cast<R>(u[4 * i]), static_cast<R>(u[4 * i + 1]), static_cast<R>(u[4 * i + 2]),
+                   static_cast<R>(u[4 * i + 3])};
+  double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+  msc_step(V, sub[i], static_cast<R>(Ea[i]), static_cast<R>(Eb[i]), static_cast<R>(sv[i]), d, x, y, z, uu);
+  od[3 * i] = d[0];
+  od[3 * i + 1] = d[1];
+  od[3 * i + 2] = d[2];
+  op[3 * i] = x;
+  op[3 * i + 1] = y;
+  op[3 * i + 2] = z;
+}
+
 int launch_status() { return cudaGetLastError() == cudaSuccess ? GV_OK : GV_ERR_CUDA; }
 
 }  // namespace
@@ -174,6 +197,17 @@ int gv_unit_distance(void *ctx, const double *pos, const double *dir, const int 
   if (n == 0) return GV_OK;
   GV_UNIT_DISPATCH((k_distance<float><<<blocks_for(n), kThreads, 0, s>>>(vf, pos, dir, sub, n, dist, next, plane)),
                    (k_distance<double><<<blocks_for(n), kThreads, 0, s>>>(vd, pos, dir, sub, n, dist, next, plane)))
+}
+
+int gv_unit_msc(void *ctx, const int *sub, const double *E_pre, const double *E_post, const double *sv,
+                const double *dir, const double *pos, const double *u, long long n, double *out_dir,
+                double *out_pos, void *stream) {
+  if (!ctx || n < 0 || (n > 0 && (!sub || !E_pre || !E_post || !sv || !dir || !pos || !u || !out_dir || !out_pos)))
+    return GV_ERR_BAD_ARG;
+  if (n == 0) return GV_OK;
+  GV_UNIT_DISPATCH(
+      (k_msc<float><<<blocks_for(n), kThreads, 0, s>>>(vf, sub, E_pre, E_post, sv, dir, pos, u, n, out_dir, out_pos)),
+      (k_msc<double><<<blocks_for(n), kThreads, 0, s>>>(vd, sub, E_pre, E_post, sv, dir, pos, u, n, out_dir, out_pos)))
 }
 
 }  // extern "C"

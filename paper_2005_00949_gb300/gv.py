@@ -96,6 +96,7 @@ def load():
             lib.gv_unit_alias_sample.argtypes = [vp, i, vp, vp, ll, vp, vp]
             lib.gv_unit_interact.argtypes = [vp, i, i, vp, vp, vp, ll, vp, vp, vp]
             lib.gv_unit_distance.argtypes = [vp, vp, vp, vp, ll, vp, vp, vp, vp]
+            lib.gv_unit_msc.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, ll, vp, vp, vp]
             _lib = lib
     return _lib
 
@@ -238,6 +239,12 @@ class Context:
         _check(self.lib.gv_unit_distance(self.h, _ptr(pos), _ptr(d), _ptr(sub), sub.numel(),
                                          _ptr(dist), _ptr(nxt), _ptr(plane), _stream_ptr(stream)),
                "gv_unit_distance")
+
+
+    def gv_unit_msc(self, sub, E_pre, E_post, s, d, pos, u, out_dir, out_pos, stream=None):
+        _check(self.lib.gv_unit_msc(self.h, _ptr(sub), _ptr(E_pre), _ptr(E_post), _ptr(s), _ptr(d), _ptr(pos),
+                                    _ptr(u), sub.numel(), _ptr(out_dir), _ptr(out_pos), _stream_ptr(stream)),
+               "gv_unit_msc")
 
 
 def gv_unit_philox(ctr, key, out, stream=None):

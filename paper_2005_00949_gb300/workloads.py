@@ -21,6 +21,7 @@ GAMMA, ELECTRON, POSITRON = 0, 1, 2
 
 P_COMPTON, P_PHOTO, P_PAIR, P_BREM, P_IONI, P_ANNIH = (1 << i for i in range(6))
 P_ALL = P_COMPTON | P_PHOTO | P_PAIR | P_BREM | P_IONI | P_ANNIH
+P_MSC = 1 << 6  # multiple scattering along charged steps (not part of P_ALL)
 
 DEFAULT_SEED = 0x6765616E7456  # "geantV"
 
@@ -164,6 +165,11 @@ def pblar_testem3(n_events: int = 1000, energy: float = 10_000.0) -> Workload:
         materials=[LEAD, LIQUID_ARGON], n_layers=50, sub_thick=[0.23, 0.57], sub_mat=[0, 1],
         half_x=20.0, half_y=20.0, nx=0, ny=0, gamma_cut=0.1, e_cut=1.0, track_cut=1e-3,
         process_mask=P_ALL, primaries=_pencil(n_events, ELECTRON, energy), n_events=n_events)
+
+
+def with_msc(wl: Workload) -> Workload:
+    """The same workload with multiple scattering along charged steps."""
+    return dataclasses.replace(wl, process_mask=wl.process_mask | P_MSC, name=wl.name + "_msc")
 
 
 CONFIGS = {

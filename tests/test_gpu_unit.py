@@ -258,3 +258,48 @@ def test_distance_matches_oracle(torch, ctx, oracle_pbps):
                 alt.append(((zb[sub[i] + 1] if d[i][2] > 0 else zb[sub[i]]) - pos[i][2]) / d[i][2])
             alt = sorted(alt)
             assert len(alt) > 1 and alt[1] - alt[0] <= 1e-5 * max(alt[0], 0.05), (i, gn[i], nx)
+
+
+# ---------------------------------------------------------------- multiple scattering
+def test_msc_matches_oracle(torch, ctx, oracle_pbps):
+    """Direction and end point after Gaussian scattering over one step, for
+    random steps in both materials, energies 1 keV - 100 GeV, step lengths up
+    to several X0 (angles up to the clamp at pi), points near boundaries."""
+    rng = np.random.default_rng(71)
+    nsub = oracle_pbps.n_subtotal()
+    zb = np.array([oracle_pbps.plane_z(k) for k in range(nsub + 1)])
+    sub = rng.integers(0, nsub, N).astype(np.int32)
+    frac = rng.uniform(0, 1, N)
+    frac[:2000] = rng.uniform(0, 1e-4, 2000)  # close to the lower plane
+    pos = np.stack([rng.uniform(-20, 20, N), rng.uniform(-20, 20, N),
+                    zb[sub] + frac * (zb[sub + 1] - zb[sub])], 1)
+    pos[2000:2100, 0] = 20.0 - rng.uniform(0, 1e-3, 100)  # close to a wall
+    Ea = 10.0 ** rng.uniform(-3, 5, N)
+    Eb = Ea * rng.uniform(0.5, 1.0, N)
+    s = 10.0 ** rng.uniform(-5, 0.5, N)
+    s[:50] = 0.0
+    c = rng.uniform(-1, 1, N)
+    ph = rng.uniform(0, 2 * math.pi, N)
+    d = np.stack([np.sqrt(1 - c * c) * np.cos(ph), np.sqrt(1 - c * c) * np.sin(ph), c], 1)
+    d[50:60] = [0, 0, 1]
+    d[60:70] = [0, 0, -1]
+    u = _u24(rng, (N, 4))
+    sub[70] = nsub  # not a sub-slab
+    od = torch.zeros((N, 3), dtype=torch.float64, device="cuda")
+    op = torch.zeros((N, 3), dtype=torch.float64, device="cuda")
+    ctx.gv_unit_msc(_dev(torch, sub), _dev(torch, Ea), _dev(torch, Eb), _dev(torch, s), _dev(torch, d),
+                    _dev(torch, pos), _dev(torch, u), od, op)
+    gd, gp = od.cpu().numpy(), op.cpu().numpy()
+    assert np.isnan(gd[70]).all() and np.isnan(gp[70]).all()
+    tol = TOL[ctx.prec]
+    sel = np.concatenate([np.arange(70), np.arange(2000, 2100),
+                          np.random.default_rng(4).choice(np.arange(71, N), 20000, False)])
+    for i in sel:
+        if i == 70:
+            continue
+        wd, wp = oracle_pbps.msc(int(sub[i]), Ea[i], Eb[i], s[i], d[i], pos[i], u[i])
+        assert np.abs(gd[i] - wd).max() <= tol, (i, gd[i], wd)
+        off_g, off_o = gp[i] - pos[i], wp - pos[i]
+        assert np.abs(off_g - off_o).max() <= tol * max(np.abs(off_o).max(), 0.05), (i, off_g, off_o)
+        # the end point stays in its sub-slab and the box
+        assert zb[sub[i]] <= gp[i][2] <= zb[sub[i] + 1] and np.abs(gp[i][:2]).max() <= 20.0

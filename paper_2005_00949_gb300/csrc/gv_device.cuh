@@ -28,6 +28,27 @@ __device__ __forceinline__ void m_sincos(double x, double *s, double *c) { sinco
 __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double m_floor(double x) { return floor(x); }
 
+// Quotients of the per-step geometry and step limits.  FP32: the fast
+// division (reciprocal times numerator, 2 ulp) instead of the IEEE-rounded
+// one, whose correction sequence costs several instructions on every step;
+// callers keep the divisor away from 0 and from the top of the range.
+__device__ __forceinline__ float q_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double q_div(double a, double b) { return a / b; }
+
+// log(1 + x) for |x| <= 0.16 in FP32: its Taylor series to x^8 (truncation
+// error below 8e-9 there, under half an FP32 ulp of the result).
+__device__ __forceinline__ float log1p_small(float x) {
+  float p = -0.125f;
+  p = fmaf(p, x, 0.14285714285714285f);
+  p = fmaf(p, x, -0.16666666666666666f);
+  p = fmaf(p, x, 0.2f);
+  p = fmaf(p, x, -0.25f);
+  p = fmaf(p, x, 0.3333333333333333f);
+  p = fmaf(p, x, -0.5f);
+  p = fmaf(p, x, 1.0f);
+  return p * x;
+}
+
 template <typename R> __device__ __forceinline__ R r_inf();
 template <> __device__ __forceinline__ float r_inf<float>() { return __int_as_float(0x7f800000); }
 template <> __device__ __forceinline__ double r_inf<double>() { return __longlong_as_double(0x7ff0000000000000ll); }
@@ -120,7 +141,9 @@ template <> __device__ __forceinline__ void grid_pos<float>(const View<float> &V
   const float l = (__log2f(E) + 9.965784284662087f) * 9.632959861247398f;
   int k = __float2int_rd(l);
   k = k < 0 ? 0 : (k > kGridN - 2 ? kGridN - 2 : k);
-  float fr = log1pf(fmaf(E, V.inv_node[k], -1.0f)) * kInvDl;
+  // E/E_k - 1 lies in [-0.07, 0.16] unless E is off the grid (clamped below)
+  const float x0 = fmaf(E, V.inv_node[k], -1.0f);
+  float fr = (x0 >= -0.16f && x0 <= 0.16f) ? log1p_small(x0) * kInvDl : log1pf(x0) * kInvDl;
   if (fr < 0.0f && k > 0) {
     --k;
     fr = log1pf(fmaf(E, V.inv_node[k], -1.0f)) * kInvDl;
@@ -172,7 +195,7 @@ template <typename R> __device__ R eloss_at(const View<R> &V, int mat, int type,
   const R Rv = Ri + f * dR;
   if (s >= Rv) return R(0);
   const R dl = static_cast<R>(2.302585092994046 / kGridPerDecade);
-  if (s <= f * dR) return E * m_exp(-dl * s / dR);
+  if (s <= f * dR) return E * m_exp(-dl * q_div(s, dR));
   const R r = Rv - s;
   const R R0 = range_at(t[0], type);
   if (r < R0) return static_cast<R>(kGridEmin) * r / R0;
@@ -263,14 +286,14 @@ __device__ __forceinline__ R distance(const View<R> &V, double x, double y, doub
     const int up = w > R(0) ? 1 : 0;
     pl = sub + up;
     nx = up ? sub + 1 : sub - 1;
-    d = static_cast<R>(V.zb[pl] - z) / w;
+    d = q_div(static_cast<R>(V.zb[pl] - z), w);
   }
   if (V.geo.walls_x && u != R(0)) {
-    const R dx = static_cast<R>(V.geo.wx[u > R(0) ? 1 : 0] - x) / u;
+    const R dx = q_div(static_cast<R>(V.geo.wx[u > R(0) ? 1 : 0] - x), u);
     if (dx < d) { d = dx; nx = -1; pl = -2; }
   }
   if (V.geo.walls_y && v != R(0)) {
-    const R dy = static_cast<R>(V.geo.wy[v > R(0) ? 1 : 0] - y) / v;
+    const R dy = q_div(static_cast<R>(V.geo.wy[v > R(0) ? 1 : 0] - y), v);
     if (dy < d) { d = dy; nx = -1; pl = -3; }
   }
   if (d < R(0)) d = R(0);

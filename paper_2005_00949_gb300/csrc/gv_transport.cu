@@ -159,7 +159,7 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   const R sig0 = s4.x, sig1 = s4.y, sig2 = (t.type == 1) ? R(0) : s4.z;
   const R Sig = sig0 + sig1 + sig2;
   const R INF = r_inf<R>();
-  const R s_phys = Sig > R(0) ? t.nlam / Sig : INF;
+  const R s_phys = Sig > R(0) ? q_div(t.nlam, Sig) : INF;
   R s_cont = INF;
   const bool charged = t.type != 0;
   if (charged) {

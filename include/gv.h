@@ -130,6 +130,10 @@ typedef struct {
   int l2_persist;             /* 1: gv_transport's step kernels read the alias tables through a persisting
                                  L2 access-policy window; the context's persisting L2 set-aside is
                                  raised to the tables' size and restored by gv_destroy */
+  int pipeline;               /* 0 (default): one fused step kernel per generation; 1: an
+                                 along-step kernel hands the tracks due a discrete interaction to
+                                 an interaction kernel that runs each warp on one (type, process)
+                                 key (needs scoring = 0; stack_capacity requests per generation) */
 } gv_config;
 
 /* A primary track; layout shared with the seeded input generator.  Its random

@@ -32,6 +32,20 @@ struct alignas(128) ClaimSlot {
   unsigned n;
 };
 
+// An interaction request of the split pipeline: the along-step kernel hands
+// a track that is due a discrete interaction to the interaction kernel
+// (one 16-byte-aligned record per request).
+template <typename R> struct alignas(16) GReq {
+  double x, y, z;
+  unsigned long long id;
+  R E, d0, d1, d2;
+  R u[6];        // u2..u7 of the step
+  unsigned ev, kk;
+  int sf;        // sub-slab | flags << 16
+  int key;       // type * 3 + process
+};
+constexpr int kNReqKey = 9;
+
 // Generation control block.  The last block of every generation writes the
 // plan of the next one; kernels only read it.
 struct Ctl {
@@ -52,6 +66,11 @@ struct Ctl {
   unsigned long long gen;
   unsigned long long live_peak;
   unsigned long long counters[16];
+  // split pipeline: requests of this generation, per key, and the claim /
+  // completion counters of the interaction kernel
+  unsigned req_n;
+  unsigned key_n[kNReqKey];
+  unsigned claim_b, blocks_done_b;
 };
 
 template <typename R> struct DevState {
@@ -72,6 +91,10 @@ template <typename R> struct DevState {
   int claim_chunks;          // chunks a warp takes per atomic claim (no basketizer)
   int along_steps;           // basketizer: steps per lane before the block basket
   int scoring;               // 0 direct atomics, 1 warp-merged (selects the kernel)
+  int pipeline;              // 0 fused step kernel, 1 along-step + interaction kernels
+  GReq<R> *req;              // split pipeline: request records [req_cap]
+  unsigned *keyidx;          // split pipeline: request indices per key [kNReqKey][req_cap]
+  unsigned long long req_cap;
   unsigned long long tail_threshold, low_water, batch, max_gen;
   int n_mat;
   unsigned xs_bytes, zb_bytes;  // staged into shared memory

@@ -463,6 +463,10 @@ template <typename R> __device__ void plan_next(const DevState<R> *S, int pn) {
   c->claim = 0;
   for (int r = 0; r < kNClaim; ++r) c->claims[r].n = 0;
   c->blocks_done = 0;
+  c->req_n = 0;
+  for (int k = 0; k < kNReqKey; ++k) c->key_n[k] = 0;
+  c->claim_b = 0;
+  c->blocks_done_b = 0;
   if (live + inj > c->live_peak) c->live_peak = live + inj;
   if (live + inj > 0) c->gen += 1;
   if (c->gen > S->max_gen && c->status == 0) c->status = GV_ERR_TIMEOUT;
@@ -835,6 +839,287 @@ __global__ void GV_STEP_BOUNDS
   }
 }
 
+// ------------------------------------------------------------------ split pipeline
+// The same generation in two kernels.  The along-step kernel runs the lanes'
+// steps until a track is due a discrete interaction, ends, or has taken its
+// along-step budget, without any block barrier after the claim; a track due
+// an interaction becomes a request record and its index goes to the list of
+// its (type, process) key.  The interaction kernel then gives every warp 32
+// requests of one key, so each warp runs one final-state model, and writes
+// survivors and secondaries to the output queues; its last block plans the
+// next generation.  The price is one request record written and read per
+// interaction.
+
+// Hand the tracks due an interaction to the interaction kernel.  All 32
+// lanes of a converged warp.
+template <typename R>
+__device__ void emit_requests(const DevState<R> *S, const Trk<R> &t, bool hand, int proc, uint32_t kstep,
+                              const R *u) {
+  if (!__ballot_sync(0xffffffffu, hand)) return;
+  Ctl *ctl = S->ctl;
+  unsigned total;
+  const unsigned slot = warp_reserve(&ctl->req_n, hand ? 1u : 0u, total);
+  const bool ok = hand && slot < S->req_cap;
+  if (hand && !ok) set_status(ctl, GV_ERR_STACK_FULL);
+  const int key = t.type * 3 + proc;
+  if (ok) {
+    GReq<R> &q = S->req[slot];
+    q.x = t.x; q.y = t.y; q.z = t.z;
+    q.id = t.id;
+    q.E = t.E; q.d0 = t.u; q.d1 = t.v; q.d2 = t.w;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) q.u[j] = u[2 + j];
+    q.ev = t.ev;
+    q.kk = kstep;
+    q.sf = t.sub | (t.flags << 16);
+    q.key = key;
+  }
+#pragma unroll
+  for (int k = 0; k < kNReqKey; ++k) {
+    const bool mine = ok && key == k;
+    if (!__ballot_sync(0xffffffffu, mine)) continue;
+    unsigned tk;
+    const unsigned pos = warp_reserve(&ctl->key_n[k], mine ? 1u : 0u, tk);
+    if (mine) S->keyidx[static_cast<size_t>(k) * S->req_cap + pos] = slot;
+  }
+}
+
+template <typename R>
+#ifndef GV_ALONG_MIN_BLOCKS
+#define GV_ALONG_MIN_BLOCKS 2
+#endif
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_ALONG_MIN_BLOCKS : 2) along_kernel(const DevState<R> *__restrict__ S, int parity) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ View<R> sV;
+  __shared__ BlockCnt bc;
+  __shared__ unsigned s_chunk, s_end[4], s_pb;
+  __shared__ int s_K;
+  Ctl *ctl = S->ctl;
+  const int tid = threadIdx.x;
+  if (ctl->done) return;
+  {  // tables, planes, 1/E_i and sub-slab materials into shared memory
+    const uint4 *src = reinterpret_cast<const uint4 *>(S->view.xs);
+    uint4 *dst = reinterpret_cast<uint4 *>(smem);
+    for (unsigned i = tid; i < S->xs_bytes / 16; i += blockDim.x) dst[i] = src[i];
+    const double *zsrc = S->view.zb;
+    double *zdst = reinterpret_cast<double *>(smem + S->xs_bytes);
+    const int nz = S->view.geo.nsub + 1;
+    for (int i = tid; i < nz; i += blockDim.x) zdst[i] = zsrc[i];
+    float *idst = reinterpret_cast<float *>(smem + S->xs_bytes + S->zb_bytes);
+    for (int i = tid; i < kGridN; i += blockDim.x) idst[i] = S->view.inv_node[i];
+    unsigned char *mdst = smem + S->xs_bytes + S->zb_bytes + kInvNodeBytes;
+    for (int i = tid; i < S->view.geo.nsub; i += blockDim.x) mdst[i] = S->view.smat[i];
+    if (tid == 0) {
+      sV = S->view;
+      sV.xs = reinterpret_cast<const V4<R> *>(smem);
+      sV.zb = zdst;
+      sV.inv_node = idst;
+      sV.smat = mdst;
+      for (int i = 0; i < 4; ++i) s_end[i] = ctl->chunk_end[i];
+      s_pb = ctl->prim_begin;
+      s_K = ctl->K;
+    }
+    if (tid < 16) bc.c[tid] = 0;
+  }
+  __syncthreads();
+  const View<R> &V = sV;
+  const int in = parity, out = parity ^ 1;
+  const unsigned cap = static_cast<unsigned>(S->capacity);
+  const unsigned n_in[3] = {min(ctl->cnt[in][0], cap), min(ctl->cnt[in][1], cap), min(ctl->cnt[in][2], cap)};
+  const unsigned n_prim_gen = ctl->prim_count;
+  for (;;) {
+    if (tid == 0) s_chunk = atomicAdd(&ctl->claim, 1u);
+    __syncthreads();
+    const unsigned chunk = s_chunk;
+    __syncthreads();
+    if (chunk >= s_end[3]) break;
+    int qsel = 0;
+    while (chunk >= s_end[qsel]) ++qsel;
+    const unsigned idx = (chunk - (qsel ? s_end[qsel - 1] : 0u)) * blockDim.x + tid;
+    Trk<R> t;
+    bool alive = false;
+    if (qsel < 3) {
+      if (idx < n_in[qsel]) {
+        const Queue<R> &q = S->q[in][qsel];
+        t.x = q.x[idx]; t.y = q.y[idx]; t.z = q.z[idx];
+        t.u = q.u[idx]; t.v = q.v[idx]; t.w = q.w[idx];
+        t.E = q.E[idx]; t.nlam = q.nlam[idx];
+        t.id = q.id[idx]; t.ev = q.ev[idx]; t.step = q.step[idx];
+        const int sf = q.sf[idx];
+        t.sub = sf & 0xffff;
+        t.flags = sf >> 16;
+        t.type = qsel;
+        alive = true;
+      }
+    } else if (idx < n_prim_gen) {
+      const unsigned i = s_pb + idx;
+      const unsigned pi = S->order ? S->order[i] : i;
+      gv_primary p = S->prim[pi];
+      if (p.type < 0 || p.type > 2 || p.event >= S->n_events) {  // caller's device array: check here
+        set_status(ctl, GV_ERR_BAD_ARG);
+        p.type = 0;
+        p.event = 0;
+        p.z = -1.0;
+        p.E_MeV = 0.0;
+      }
+      t.type = p.type;
+      t.E = static_cast<R>(p.E_MeV);
+      t.x = p.x; t.y = p.y; t.z = p.z;
+      t.u = static_cast<R>(p.u); t.v = static_cast<R>(p.v); t.w = static_cast<R>(p.w);
+      t.nlam = R(-1);
+      t.id = p.id;
+      t.ev = p.event;
+      t.step = 0;
+      t.flags = kFlagPrimary;
+      t.sub = locate(V.zb, V.geo.nsub, p.z, p.w);
+      count(S, &bc, t.ev, GV_C_TRK_G + t.type);
+      if (t.sub < 0) {
+        atomicAdd(&S->escape[t.ev], p.E_MeV);
+        if (t.type == 2) count(S, &bc, t.ev, GV_C_EP_ESC);
+      } else {
+        alive = true;
+        if (atomicAdd(&S->evlive[t.ev], 1u) == 0u) atomicAdd(&ctl->ev_started, 1u);
+      }
+    }
+    const int K = s_K;
+    for (int kk = 0; kk < K; ++kk) {
+      if (!__any_sync(0xffffffffu, alive)) break;
+      const bool was_alive = alive;
+      Kids<R> kids;
+      kids.n = 0;
+      uint32_t kstep = 0;
+      int proc = -1, lim = -1;
+      R u[8];
+      unsigned n_st = 0, n_geom = 0, n_iter = 0;
+      for (int m = 0; m < S->along_steps && alive && proc < 0; ++m) {
+        ++n_iter;
+        const uint32_t before = t.step;
+        alive = step_track(V, S, t, kids, kstep, &bc, proc, u, lim, static_cast<Pending<R> *>(nullptr)) != 0;
+        if (!(t.E == t.E) || (__double2hiint(t.z) & 0x7ff00000) == 0x7ff00000) {
+          set_status(ctl, GV_ERR_NUMERIC);
+          alive = false;
+          proc = -1;
+        }
+        if (t.step != before) {
+          ++n_st;
+          n_geom += lim == 0 ? 1u : 0u;
+        }
+      }
+      push_kids(S, out, parent_of(t), kids, kstep, &bc);
+      {  // step counters, one shared-memory atomic per warp and kind
+        const unsigned wst = __reduce_add_sync(0xffffffffu, n_st);
+        const unsigned wiq = __reduce_max_sync(0xffffffffu, n_iter);
+        if (wst) {
+          const unsigned wg = __reduce_add_sync(0xffffffffu, t.type == 0 ? n_st : 0u);
+          const unsigned we = __reduce_add_sync(0xffffffffu, t.type == 1 ? n_st : 0u);
+          const unsigned wx = __reduce_add_sync(0xffffffffu, (n_st && alive && proc >= 0) ? 1u : 0u);
+          const unsigned wb = __reduce_add_sync(0xffffffffu, n_geom);
+          if ((tid & 31) == 0) {
+            atomicAdd(&bc.c[GV_C_STEPS], static_cast<unsigned long long>(wst));
+            if (wg) atomicAdd(&bc.c[GV_C_STEPS_G], static_cast<unsigned long long>(wg));
+            if (we) atomicAdd(&bc.c[GV_C_STEPS_EM], static_cast<unsigned long long>(we));
+            if (wst - wg - we) atomicAdd(&bc.c[GV_C_STEPS_EP], static_cast<unsigned long long>(wst - wg - we));
+            if (wx) atomicAdd(&bc.c[GV_C_DISCRETE], static_cast<unsigned long long>(wx));
+            if (wb) atomicAdd(&bc.c[GV_C_GEOM], static_cast<unsigned long long>(wb));
+          }
+        }
+        if ((tid & 31) == 0 && wiq) atomicAdd(&bc.c[GV_C_LANE_SLOTS], 32ull * wiq);
+      }
+      if (was_alive && !alive) track_ended(S, t.ev);
+      const bool hand = alive && proc >= 0;
+      emit_requests(S, t, hand, proc, kstep, u);
+      alive = alive && !hand;  // the interaction kernel owns it now
+    }
+    push_survivor(S, out, t, alive);
+  }
+  __syncthreads();
+  if (tid < 16 && bc.c[tid]) atomicAdd(&ctl->counters[tid], bc.c[tid]);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) interact_kernel(const DevState<R> *__restrict__ S, int parity) {
+  __shared__ View<R> sV;
+  __shared__ BlockCnt bc;
+  __shared__ unsigned s_kend[kNReqKey], s_kn[kNReqKey];
+  __shared__ int s_last;
+  Ctl *ctl = S->ctl;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (ctl->done) return;
+  if (tid == 0) {
+    sV = S->view;  // tables stay in global memory: the final states read the alias bins only
+    unsigned acc = 0;
+    for (int k = 0; k < kNReqKey; ++k) {
+      const unsigned n = min(ctl->key_n[k], static_cast<unsigned>(S->req_cap));
+      s_kn[k] = n;
+      acc += (n + 31u) / 32u;
+      s_kend[k] = acc;
+    }
+  }
+  if (tid < 16) bc.c[tid] = 0;
+  __syncthreads();
+  const View<R> &V = sV;
+  const int out = parity ^ 1;
+  for (;;) {
+    unsigned chunk = 0;
+    if (lane == 0) chunk = atomicAdd(&ctl->claim_b, 1u);
+    chunk = __shfl_sync(0xffffffffu, chunk, 0);
+    if (chunk >= s_kend[kNReqKey - 1]) break;
+    int k = 0;
+    while (chunk >= s_kend[k]) ++k;
+    const unsigned pos = (chunk - (k ? s_kend[k - 1] : 0u)) * 32u + lane;
+    const bool has = pos < s_kn[k];
+    const int ty = k / 3, proc = k - 3 * ty;
+    Trk<R> t;
+    Kids<R> kids;
+    kids.n = 0;
+    Parent par;
+    uint32_t kk = 0;
+    bool alive = false;
+    if (has) {
+      const GReq<R> q = S->req[S->keyidx[static_cast<size_t>(k) * S->req_cap + pos]];
+      R uu[8] = {R(0), R(0), q.u[0], q.u[1], q.u[2], q.u[3], q.u[4], q.u[5]};
+      R d[3] = {q.d0, q.d1, q.d2};
+      R e = q.E;
+      t.x = q.x; t.y = q.y; t.z = q.z;
+      t.id = q.id;
+      t.ev = q.ev;
+      t.sub = q.sf & 0xffff;
+      t.flags = q.sf >> 16;
+      t.type = ty;
+      kk = q.kk;
+      t.step = kk + 1;
+      t.nlam = R(-1);
+      const int r = final_state(V, S, &bc, ty, proc, e, d, uu, kids, t.ev, t.sub, t.x, t.y);
+      t.E = e;
+      t.u = d[0]; t.v = d[1]; t.w = d[2];
+      if (r >= 0) t.flags |= kFlagInteracted;
+      alive = r != 0;
+      par = parent_of(t);
+    } else {
+      par.x = par.y = par.z = 0.0;
+      par.id = 0;
+      par.ev = 0;
+      par.sub = 0;
+    }
+    push_kids(S, out, par, kids, kk, &bc);
+    if (has && !alive) track_ended(S, t.ev);
+    push_survivor(S, out, t, alive);
+  }
+  __syncthreads();
+  if (tid < 16 && bc.c[tid]) atomicAdd(&ctl->counters[tid], bc.c[tid]);
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const unsigned d = atomicAdd(&ctl->blocks_done_b, 1u);
+    s_last = (d == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last && tid == 0) {
+    __threadfence();
+    plan_next(S, out);
+  }
+}
+
 }  // namespace gv
 
 // ====================================================================== host
@@ -876,7 +1161,10 @@ struct Ctx {
   int last_status = 0;
   ModelMeta meta[kNModel];
   size_t xs_bytes = 0, zb_bytes = 0, smem_bytes = 0, req_off = 0, bins_bytes = 0;
-  int grid = 0;
+  int grid = 0, grid_b = 0;
+  // split pipeline: interaction requests and their per-key index lists
+  void *d_req = nullptr;
+  unsigned *d_keyidx = nullptr;
   // L2 persisting window over the alias bins (config l2_persist)
   size_t l2_window = 0, l2_old_limit = 0;
 };
@@ -927,6 +1215,7 @@ int validate_cfg(const gv_config &c) {
   if (c.along_steps < 1 || c.along_steps > 64) return GV_ERR_BAD_ARG;
   if (c.scoring < 0 || c.scoring > 1) return GV_ERR_BAD_ARG;
   if (c.l2_persist < 0 || c.l2_persist > 1) return GV_ERR_BAD_ARG;
+  if (c.pipeline < 0 || c.pipeline > 1 || (c.pipeline == 1 && c.scoring != 0)) return GV_ERR_BAD_ARG;
   return GV_OK;
 }
 
@@ -1088,6 +1377,23 @@ template <typename R> int prepare_device(Ctx *c) {
   CK(cudaMallocHost(&c->h_ctl, sizeof(Ctl)));
   c->zb_bytes = ((c->nsub + 1) * sizeof(double) + 15) / 16 * 16;
   c->req_off = c->xs_bytes + c->zb_bytes + kInvNodeBytes + (c->nsub + 15) / 16 * 16;
+  if (c->cfg.pipeline) {
+    const size_t rc_ = static_cast<size_t>(cap);
+    if (cudaMalloc(&c->d_req, rc_ * sizeof(GReq<R>)) != cudaSuccess ||
+        cudaMalloc(&c->d_keyidx, rc_ * kNReqKey * sizeof(unsigned)) != cudaSuccess)
+      return GV_ERR_OOM;
+    c->smem_bytes = c->req_off;
+    const void *ka = reinterpret_cast<const void *>(along_kernel<R>);
+    const void *kb = reinterpret_cast<const void *>(interact_kernel<R>);
+    CK(cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(c->smem_bytes)));
+    int occ = 0, occ_b = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ka, c->cfg.block_size, c->smem_bytes));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, kb, 256, 0));
+    if (occ < 1 || occ_b < 1) return GV_ERR_BAD_ARG;
+    c->grid = c->sm_count * std::min(occ, c->cfg.blocks_per_sm);
+    c->grid_b = c->sm_count * occ_b;
+    return GV_OK;
+  }
   c->smem_bytes = c->req_off + (c->cfg.process_sort ? sizeof(IReq<R>) * c->cfg.block_size : 0);
   const void *kern = reinterpret_cast<const void *>(pick_step_kernel<R>(c->cfg));
   CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(c->smem_bytes)));
@@ -1108,10 +1414,14 @@ template <typename R> DevState<R> make_state(Ctx *c) {
   s.capacity = static_cast<unsigned long long>(c->cfg.stack_capacity);
   s.ctl = c->d_ctl;
   s.block_size = c->cfg.block_size;
-  s.chunk = (c->cfg.process_sort || c->cfg.claim_chunks == 0) ? c->cfg.block_size : 32;
+  s.chunk = (c->cfg.pipeline || c->cfg.process_sort || c->cfg.claim_chunks == 0) ? c->cfg.block_size : 32;
   s.claim_chunks = c->cfg.claim_chunks;
   s.along_steps = c->cfg.along_steps;
   s.scoring = c->cfg.scoring;
+  s.pipeline = c->cfg.pipeline;
+  s.req = reinterpret_cast<GReq<R> *>(c->d_req);
+  s.keyidx = c->d_keyidx;
+  s.req_cap = c->d_req ? static_cast<unsigned long long>(c->cfg.stack_capacity) : 0ull;
   s.mode = c->cfg.mode;
   s.K_bulk = c->cfg.steps_per_claim;
   s.K_tail = c->cfg.tail_steps_per_claim;
@@ -1131,9 +1441,16 @@ template <typename R> int capture_graph(Ctx *c) {
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
   const DevState<R> *S = reinterpret_cast<const DevState<R> *>(c->d_state);
-  const StepFn<R> step = pick_step_kernel<R>(c->cfg);
-  for (int i = 0; i < c->cfg.generations_per_graph; ++i)
-    step<<<c->grid, c->cfg.block_size, c->smem_bytes, c->stream>>>(S, i & 1);
+  if (c->cfg.pipeline) {
+    for (int i = 0; i < c->cfg.generations_per_graph; ++i) {
+      along_kernel<R><<<c->grid, c->cfg.block_size, c->smem_bytes, c->stream>>>(S, i & 1);
+      interact_kernel<R><<<c->grid_b, 256, 0, c->stream>>>(S, i & 1);
+    }
+  } else {
+    const StepFn<R> step = pick_step_kernel<R>(c->cfg);
+    for (int i = 0; i < c->cfg.generations_per_graph; ++i)
+      step<<<c->grid, c->cfg.block_size, c->smem_bytes, c->stream>>>(S, i & 1);
+  }
   cudaError_t e = cudaStreamEndCapture(c->stream, &g);
   if (e != cudaSuccess) return GV_ERR_CUDA;
   if (c->l2_window) {  // the window rides on every captured step launch
@@ -1272,7 +1589,7 @@ int run_transport(Ctx *c, const gv_primary *p, long long n, long long n_events, 
     CK(cudaEventRecord(c->t0, c->stream));
     for (int i = 0; i < between; ++i) CK(cudaGraphLaunch(c->graph, c->stream));
     CK(cudaEventRecord(c->t1, c->stream));
-    launches += static_cast<long long>(between) * c->cfg.generations_per_graph;
+    launches += static_cast<long long>(between) * c->cfg.generations_per_graph * (c->cfg.pipeline ? 2 : 1);
     CK(cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     float ms = 0.f;
@@ -1336,6 +1653,7 @@ int gv_default_config(gv_config *cfg) {
   cfg->along_steps = 4;
   cfg->scoring = 0;
   cfg->l2_persist = 0;
+  cfg->pipeline = 0;
   return GV_OK;
 }
 
@@ -1455,6 +1773,8 @@ void gv_destroy(void *ctx) {
   cudaFree(c->d_evlive);
   cudaFree(c->d_prim);
   cudaFree(c->d_order);
+  cudaFree(c->d_req);
+  cudaFree(c->d_keyidx);
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);

@@ -87,9 +87,10 @@ def test_photon_slab_transmission(gvmod, oracle_mod, prec):
 
 
 # ---------------------------------------------------------------- FP64 event-by-event
-def test_fp64_showers_follow_oracle_event_by_event(gvmod, oracle_mod):
+@pytest.mark.parametrize("pipeline", [0, 1], ids=["fused", "split"])
+def test_fp64_showers_follow_oracle_event_by_event(gvmod, oracle_mod, pipeline):
     wl = W.pbps_electrons(300, 1000.0)
-    ctx = _ctx(gvmod, wl, precision=1, per_event_counts=1)
+    ctx = _ctx(gvmod, wl, precision=1, per_event_counts=1, pipeline=pipeline)
     r = ctx.transport(per_event=True)
     assert r["status"] == 0
     ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
@@ -182,7 +183,9 @@ def test_integer_counts_invariant_to_launch_shape(gvmod):
               dict(process_sort=0, claim_chunks=1, block_size=128),
               dict(mode=1), dict(scoring=1), dict(scoring=1, along_steps=1),
               dict(process_sort=0, claim_chunks=0, scoring=1), dict(process_sort=0, scoring=1),
-              dict(l2_persist=1), dict(l2_persist=1, scoring=1, mode=1)]
+              dict(l2_persist=1), dict(l2_persist=1, scoring=1, mode=1),
+              dict(pipeline=1), dict(pipeline=1, along_steps=1, steps_per_claim=3),
+              dict(pipeline=1, mode=1, block_size=128)]
     for kw in shapes:
         ctx = _ctx(gvmod, wl, per_event_counts=1, **kw)
         r = ctx.transport(per_event=True)
@@ -198,7 +201,8 @@ def test_integer_counts_invariant_to_launch_shape(gvmod):
         # before the FP64 atomic
         scale = np.maximum(base["edep"].sum(1, keepdims=True), 1.0)
         rel = (np.abs(r["edep"] - base["edep"]) / scale).max()
-        other_kernel = kw.get("process_sort", 1) != 1 or kw.get("scoring", 0) != 0
+        other_kernel = (kw.get("process_sort", 1) != 1 or kw.get("scoring", 0) != 0
+                        or kw.get("pipeline", 0) != 0)
         assert rel < (1e-5 if other_kernel else 1e-9), (kw, rel)
         ctx.close()
 

@@ -50,7 +50,7 @@ class OrSetup(C.Structure):
                 ("n_sub", C.c_int), ("sub_thick", C.c_double * 8), ("sub_mat", C.c_int * 8),
                 ("half_x", C.c_double), ("half_y", C.c_double), ("nx", C.c_int), ("ny", C.c_int),
                 ("gamma_cut", C.c_double), ("e_cut", C.c_double), ("track_cut", C.c_double),
-                ("process_mask", C.c_uint)]
+                ("process_mask", C.c_uint), ("field_T", C.c_double), ("field_axis", C.c_int)]
 
 
 def _load():
@@ -103,6 +103,9 @@ def _load():
             lib.or_msc_theta0.restype = d
             lib.or_msc_theta0.argtypes = [p, i, d, d]
             lib.or_msc.argtypes = [p, i, d, d, d, p, p, p, p, p]
+            lib.or_field_step_limit.restype = d
+            lib.or_field_step_limit.argtypes = [p, i, d, p]
+            lib.or_helix.argtypes = [p, i, d, d, p, p, p]
             lib.or_transport.argtypes = [p, p, C.c_long, C.c_long, C.c_uint64, p, p, p, p, i]
             _lib = lib
     return _lib
@@ -150,6 +153,7 @@ class Oracle:
         s.half_x, s.half_y, s.nx, s.ny = wl.half_x, wl.half_y, wl.nx, wl.ny
         s.gamma_cut, s.e_cut, s.track_cut = wl.gamma_cut, wl.e_cut, wl.track_cut
         s.process_mask = wl.process_mask
+        s.field_T, s.field_axis = wl.field_T, wl.field_axis
         self._setup = s
         h = C.c_void_p()
         rc = lib.or_create(C.byref(s), C.byref(h))
@@ -274,6 +278,18 @@ class Oracle:
         od, op = np.zeros(3), np.zeros(3)
         self.lib.or_msc(self.h, sub, E_pre, E_post, s, _ptr(dd), _ptr(pp), _ptr(uu), _ptr(od), _ptr(op))
         return od, op
+
+    # -- magnetic field
+    def field_step_limit(self, ptype: int, E: float, d) -> float:
+        dd = np.ascontiguousarray(d, dtype=np.float64)
+        return self.lib.or_field_step_limit(self.h, ptype, E, _ptr(dd))
+
+    def helix(self, ptype: int, E: float, s: float, d):
+        """(displacement, new direction) along the helix after a path s."""
+        dd = np.ascontiguousarray(d, dtype=np.float64)
+        dp, nd = np.zeros(3), np.zeros(3)
+        self.lib.or_helix(self.h, ptype, E, s, _ptr(dd), _ptr(dp), _ptr(nd))
+        return dp, nd
 
     # -- transport
     def transport(self, primaries=None, n_events=None, seed=None, n_threads: int = 1,

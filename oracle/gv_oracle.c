@@ -698,6 +698,61 @@ double or_safety(const or_ctx *c, const double pos[3], int sub) {
 }
 
 /* ------------------------------------------------------------------ */
+/* uniform magnetic field (the field propagation of Sec. 3.6)          */
+/* ------------------------------------------------------------------ */
+/* A track of charge q and momentum p (MeV/c) in a field B (tesla) along the
+ * unit vector b turns at the rate dd/ds = q k (d x b), k = c B / p with
+ * c = 2.99792458 cm^-1 MeV/(c T) (the radius of curvature of 1 MeV/c in 1 T
+ * is 0.33356 cm).  Splitting d = a + c0 with a = (d.b) b, and g = c0 x b,
+ * the exact helix after a path s, th = q k s, is
+ *   position  r0 + a s + c0 sin(th) / (q k) + g (1 - cos th) / (q k)
+ *   direction a + c0 cos(th) + g sin(th).                                 */
+#define FIELD_C 2.99792458
+#define FIELD_SAGITTA 1e-3 /* cm */
+#define FIELD_MAX_TURN 0.2 /* rad */
+
+static double field_curvature(const or_ctx *c, int type, double E) {
+  const double p = sqrt(E * (E + 2.0 * ME));
+  const double q = type == OR_POSITRON ? 1.0 : -1.0;
+  return q * FIELD_C * c->s.field_T / p;
+}
+
+/* Longest step with a chord sagitta <= 10 um and a turn <= 0.2 rad, taking
+ * the curvature of the helix itself, |k| sin(angle between d and b). */
+double or_field_step_limit(const or_ctx *c, int type, double E, const double dir[3]) {
+  if (type == OR_GAMMA || c->s.field_T == 0.0) return INFINITY;
+  const double db = dir[c->s.field_axis];
+  const double keff = fabs(field_curvature(c, type, E)) * sqrt(fmax(0.0, 1.0 - db * db));
+  if (!(keff > 0.0)) return INFINITY;
+  return fmin(sqrt(8.0 * FIELD_SAGITTA / keff), FIELD_MAX_TURN / keff);
+}
+
+void or_helix(const or_ctx *c, int type, double E, double s, const double dir[3], double dpos[3],
+              double ndir[3]) {
+  const int ax = c->s.field_axis;
+  double b[3] = {0.0, 0.0, 0.0};
+  b[ax] = 1.0;
+  const double db = dir[ax];
+  double a[3], c0[3], g[3];
+  for (int j = 0; j < 3; ++j) {
+    a[j] = db * b[j];
+    c0[j] = dir[j] - a[j];
+  }
+  g[0] = c0[1] * b[2] - c0[2] * b[1];
+  g[1] = c0[2] * b[0] - c0[0] * b[2];
+  g[2] = c0[0] * b[1] - c0[1] * b[0];
+  const double w = (type == OR_GAMMA || c->s.field_T == 0.0) ? 0.0 : field_curvature(c, type, E);
+  const double th = w * s;
+  /* sin(th)/th and (1 - cos th)/th = 2 sin^2(th/2)/th, both -> their limits at 0 */
+  const double sc = th != 0.0 ? sin(th) / th : 1.0;
+  const double cc = th != 0.0 ? 2.0 * sin(0.5 * th) * sin(0.5 * th) / th : 0.0;
+  for (int j = 0; j < 3; ++j) {
+    dpos[j] = a[j] * s + c0[j] * s * sc + g[j] * s * cc;
+    ndir[j] = a[j] + c0[j] * cos(th) + g[j] * sin(th);
+  }
+}
+
+/* ------------------------------------------------------------------ */
 /* multiple Coulomb scattering (the MSC stages of Sec. 2.1.2)          */
 /* ------------------------------------------------------------------ */
 /* Highland width of the projected angle for a unit-charge track of kinetic
@@ -1115,6 +1170,8 @@ static void run_event(const job_t *J, long ev, ostack *st) {
       if (charged) {
         double R = or_table_lookup(c, t.type, t.type == OR_ELECTRON ? 2 : 3, mat, t.E);
         s_cont = fmax(STEP_ALPHA_R * R, fmin(STEP_RHO_F, R));
+        /* the field's step limit acts like the continuous one */
+        s_cont = fmin(s_cont, or_field_step_limit(c, t.type, t.E, t.dir));
       }
       /* GeomQuery */
       int next, plane;
@@ -1126,16 +1183,28 @@ static void run_event(const job_t *J, long ev, ostack *st) {
         if (t.type == OR_POSITRON) cnt[OR_C_EP_ESC] += 1;
         break;
       }
-      /* Propagation */
+      /* Propagation: straight, or the helix of the pre-step momentum */
       double mid[3], pre_pos[3] = {t.pos[0], t.pos[1], t.pos[2]};
-      for (int j = 0; j < 3; ++j) {
-        mid[j] = pre_pos[j] + 0.5 * sstep * t.dir[j];
-        t.pos[j] = pre_pos[j] + sstep * t.dir[j];
+      const double pre_dir[3] = {t.dir[0], t.dir[1], t.dir[2]};
+      if (charged && s->field_T != 0.0) {
+        double dp[3], dh[3], nd[3], tmp[3];
+        or_helix(c, t.type, t.E, sstep, t.dir, dp, nd);
+        or_helix(c, t.type, t.E, 0.5 * sstep, t.dir, dh, tmp);
+        for (int j = 0; j < 3; ++j) {
+          mid[j] = pre_pos[j] + dh[j];
+          t.pos[j] = pre_pos[j] + dp[j];
+          t.dir[j] = nd[j];
+        }
+      } else {
+        for (int j = 0; j < 3; ++j) {
+          mid[j] = pre_pos[j] + 0.5 * sstep * t.dir[j];
+          t.pos[j] = pre_pos[j] + sstep * t.dir[j];
+        }
       }
       if (lim == 0) {
         if (plane >= 0) t.pos[2] = c->zb[plane];
-        else if (plane == -2) t.pos[0] = t.dir[0] > 0.0 ? s->half_x : -s->half_x;
-        else if (plane == -3) t.pos[1] = t.dir[1] > 0.0 ? s->half_y : -s->half_y;
+        else if (plane == -2) t.pos[0] = pre_dir[0] > 0.0 ? s->half_x : -s->half_x;
+        else if (plane == -3) t.pos[1] = pre_dir[1] > 0.0 ? s->half_y : -s->half_y;
       }
       if (Sig > 0.0) t.nlam = (lim == 1) ? 0.0 : t.nlam - sstep * Sig;
       t.step = k + 1;

@@ -20,6 +20,10 @@
  *   annihilation     Heitler two-photon, in flight and at rest
  *   multiple scatt.  optional (OR_P_MSC): Gaussian angle of Highland width
  *                    and correlated lateral offset, within the safety
+ *   magnetic field   optional uniform field along a coordinate axis: charged
+ *                    tracks follow the exact helix of their pre-step momentum,
+ *                    their steps limited to a 10 um sagitta and 0.2 rad;
+ *                    boundaries are found along the straight line
  * The stepping loop follows the stage sequence of Sec. 2.1.2 (Fig. "simulation
  * stages"): PreStep, ComputeIntLen, GeomQuery, Propagation, AlongStepAction,
  * PostStepActions, SteppingActions; secondaries go to a LIFO stack (the
@@ -77,6 +81,8 @@ typedef struct {
   int nx, ny;                       /* scoring cells per layer (0: none) */
   double gamma_cut, e_cut, track_cut; /* MeV */
   unsigned process_mask;
+  double field_T;                   /* uniform magnetic field, tesla (0: none) */
+  int field_axis;                   /* its direction: 0 x, 1 y, 2 z */
 } or_setup;
 
 typedef struct {
@@ -126,6 +132,11 @@ int or_locate(const or_ctx *c, double z, double w);
 double or_distance(const or_ctx *c, const double pos[3], const double dir[3], int sub,
                    int *next_sub, int *plane);
 double or_safety(const or_ctx *c, const double pos[3], int sub);
+
+/* --- uniform magnetic field: helix of a charged track (type 1 e-, 2 e+) */
+double or_field_step_limit(const or_ctx *c, int type, double E, const double dir[3]);
+void or_helix(const or_ctx *c, int type, double E, double s, const double dir[3], double dpos[3],
+              double ndir[3]);
 
 /* --- multiple scattering (Highland width, Gaussian angle and offset) -- */
 double or_msc_theta0(const or_ctx *c, int mat, double T, double s);

@@ -62,6 +62,8 @@ class Workload:
     primaries: np.ndarray  # PRIMARY_DTYPE
     n_events: int
     seed: int = DEFAULT_SEED
+    field_T: float = 0.0  # uniform magnetic field (tesla) along field_axis (0 x, 1 y, 2 z)
+    field_axis: int = 1
 
     @property
     def n_sub(self) -> int:
@@ -165,6 +167,12 @@ def pblar_testem3(n_events: int = 1000, energy: float = 10_000.0) -> Workload:
         materials=[LEAD, LIQUID_ARGON], n_layers=50, sub_thick=[0.23, 0.57], sub_mat=[0, 1],
         half_x=20.0, half_y=20.0, nx=0, ny=0, gamma_cut=0.1, e_cut=1.0, track_cut=1e-3,
         process_mask=P_ALL, primaries=_pencil(n_events, ELECTRON, energy), n_events=n_events)
+
+
+def with_field(wl: Workload, tesla: float = 4.0, axis: int = 1) -> Workload:
+    """The same workload in a uniform magnetic field (default: 4 T along y,
+    transverse to the beam, as in the paper's TestEm3 set-up)."""
+    return dataclasses.replace(wl, field_T=tesla, field_axis=axis, name=f"{wl.name}_B{tesla:g}T{'xyz'[axis]}")
 
 
 def with_msc(wl: Workload) -> Workload:

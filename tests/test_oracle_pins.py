@@ -581,3 +581,81 @@ def test_msc_special_cases_and_safety(oracle_mod):
         assert zb[sub] <= npos[2] <= zb[sub + 1]
         assert abs(npos[0]) <= 20.0 and abs(npos[1]) <= 20.0
         assert np.linalg.norm(npos - pos) <= 0.99 * o.safety(pos, sub) + 1e-12  # pos ~ 20: ulp 4e-15
+
+
+# ---------------------------------------------------------------- magnetic field
+# The closed-form helix against a numerical integration of the equation of
+# motion dr/ds = d, dd/ds = q k (d x b) (classical Runge-Kutta, 2e4 steps),
+# with k = 2.99792458 B / p cm^-1 (p in MeV/c, B in tesla): independent of
+# the closed form.  The step limit keeps the chord's sagitta within 10 um.
+def _rk4_helix(q, k, b, d, s, n=20_000):
+    b = np.asarray(b, float)
+    r = np.zeros(3)
+    v = np.asarray(d, float).copy()
+    h = s / n
+
+    def f(vv):
+        return q * k * np.cross(vv, b)
+
+    for _ in range(n):
+        k1r, k1v = v, f(v)
+        k2r, k2v = v + 0.5 * h * k1v, f(v + 0.5 * h * k1v)
+        k3r, k3v = v + 0.5 * h * k2v, f(v + 0.5 * h * k2v)
+        k4r, k4v = v + h * k3v, f(v + h * k3v)
+        r = r + h / 6 * (k1r + 2 * k2r + 2 * k3r + k4r)
+        v = v + h / 6 * (k1v + 2 * k2v + 2 * k3v + k4v)
+    return r, v
+
+
+@pytest.mark.parametrize("ptype,E,d,s", [
+    (W.ELECTRON, 10.0, (0.0, 0.0, 1.0), 0.3),
+    (W.POSITRON, 10.0, (0.0, 0.0, 1.0), 0.3),
+    (W.ELECTRON, 2.0, (0.3, 0.5, math.sqrt(0.66)), 0.05),
+    (W.POSITRON, 0.5, (0.6, -0.64, 0.48), 0.4),   # several turns
+    (W.ELECTRON, 5000.0, (0.1, 0.0, math.sqrt(0.99)), 2.0),
+])
+def test_helix_matches_integrated_motion(oracle_mod, ptype, E, d, s):
+    wl = W.with_field(W.pbps_electrons(1), 4.0, 1)
+    o = oracle_mod.Oracle(wl)
+    p = math.sqrt(E * (E + 2 * ME))
+    q = 1.0 if ptype == W.POSITRON else -1.0
+    dp, nd = o.helix(ptype, E, s, d)
+    r, v = _rk4_helix(q, 2.99792458 * 4.0 / p, (0.0, 1.0, 0.0), d, s)
+    assert np.abs(dp - r).max() < 1e-9 * max(1.0, s)
+    assert np.abs(nd - v).max() < 1e-9
+    assert abs(np.linalg.norm(nd) - 1.0) < 1e-14 and abs(nd[1] - d[1]) < 1e-15
+
+
+def test_field_step_limit_bounds_sagitta_and_turn(oracle_mod):
+    wl = W.with_field(W.pbps_electrons(1), 4.0, 1)
+    o = oracle_mod.Oracle(wl)
+    rng = np.random.default_rng(8)
+    for _ in range(200):
+        E = 10.0 ** rng.uniform(-2, 4)
+        ptype = int(rng.integers(1, 3))
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        s = o.field_step_limit(ptype, E, d)
+        end, nd = o.helix(ptype, E, s, d)
+        chord = end / np.linalg.norm(end)
+        sag = max(np.linalg.norm(o.helix(ptype, E, f * s, d)[0] - (o.helix(ptype, E, f * s, d)[0] @ chord) * chord)
+                  for f in np.linspace(0, 1, 101))
+        assert sag <= 1e-3 * (1 + 1e-6)
+        assert math.acos(min(1.0, float(nd @ d))) <= 0.2 + 1e-9
+    assert o.field_step_limit(W.GAMMA, 1.0, [0, 0, 1]) == math.inf
+    assert o.field_step_limit(W.ELECTRON, 1.0, [0, 1, 0]) == math.inf  # along the field
+    plain = oracle_mod.Oracle(W.pbps_electrons(1))
+    assert plain.field_step_limit(W.ELECTRON, 1.0, [0, 0, 1]) == math.inf
+
+
+def test_transport_in_field_conserves_energy_and_charge(oracle_mod):
+    wl = W.with_msc(W.with_field(W.pblar_testem3(20, 2000.0), 4.0, 1))
+    r = oracle_mod.Oracle(wl).transport(n_threads=4)
+    c = r["counts"]
+    T0 = wl.primaries["E"]
+    res = (r["edep"].sum(1) + r["escape"] - (T0 + 2 * ME * (c[:, 8] - c[:, 7]))) / T0
+    assert np.abs(res).max() < 1e-9
+    assert np.all(c[:, 7] == c[:, 8] + c[:, 9])
+    # the field bends charged tracks: more steps than without it
+    plain = oracle_mod.Oracle(W.with_msc(W.pblar_testem3(20, 2000.0))).transport(n_threads=4)
+    assert c[:, 0].sum() > plain["counts"][:, 0].sum()

@@ -80,7 +80,11 @@ typedef struct {
 /* Layered box along +z from z = 0: n_layers repetitions of n_sub sub-slabs
  * (thickness sub_thick_cm[j], material sub_mat[j]).  Transverse half widths
  * half_x_cm/half_y_cm (<= 0: unbounded).  nx_cells x ny_cells scoring cells per
- * layer over the full transverse extent (0: no cell scoring). */
+ * layer over the full transverse extent (0: no cell scoring).  An optional
+ * uniform magnetic field of field_T tesla along the axis field_axis (0 x,
+ * 1 y, 2 z; field propagation, Sec. 3.6): charged tracks follow the exact
+ * helix of their pre-step momentum, with steps limited to a 10 um chord
+ * sagitta and a 0.2 rad turn; boundaries are found along the straight line. */
 typedef struct {
   int n_layers;
   int n_sub;
@@ -88,6 +92,8 @@ typedef struct {
   int sub_mat[GV_MAX_SUB];
   double half_x_cm, half_y_cm;
   int nx_cells, ny_cells;
+  double field_T;
+  int field_axis;
 } gv_layers;
 
 /* Production cuts (MeV): gamma_cut splits bremsstrahlung into continuous and
@@ -123,7 +129,8 @@ typedef struct {
                                  32-track chunks from 16 sliced counters; 0 = one claim per block */
   int along_steps;            /* with process_sort: steps a track may take without a discrete
                                  interaction before its block baskets the interactions (1..64) */
-  int scoring;                /* energy tallies: 0 (default) = one FP64 atomic per deposit;
+  int scoring;                /* energy tallies (1 is not available with a field):
+                                 0 (default) = one FP64 atomic per deposit;
                                  1 = a lane merges consecutive deposits to the same (event,
                                  sub-slab) in a compensated sum, and after every step round its
                                  warp adds equal keys together before one FP64 atomic per key */
@@ -207,7 +214,7 @@ int gv_transport(void *ctx, const gv_primary *p, long long n, long long n_events
  *   counters  host array of 16 (as gv_result.counters).
  * Runs the batched schedule with at most 64 events in flight, on `stream`,
  * and returns when done.  GV_ERR_BAD_ARG: n_events > 65,536, host pointers,
- * or an FP64 context; GV_ERR_STACK_FULL: more live tracks than the array
+ * an FP64 context, or a context with a magnetic field; GV_ERR_STACK_FULL: more live tracks than the array
  * holds (showers far above ~10 GeV per event in flight). */
 int gv_transport_static(void *ctx, const gv_primary *prim, long long n, long long n_events,
                         unsigned long long seed, void *stream, double *edep, double *escape_E,
@@ -273,6 +280,13 @@ int gv_unit_interact(void *ctx, int type, int proc, const double *E, const doubl
 int gv_unit_msc(void *ctx, const int *sub, const double *E_pre, const double *E_post, const double *s,
                 const double *dir, const double *pos, const double *u, long long n, double *out_dir,
                 double *out_pos, void *stream);
+
+/* Helix of a charged track in the context's field: for each i, a track of
+ * type `type` (1 e-, 2 e+) and kinetic energy E[i] moving along dir[3i..]
+ * for a path s[i]; out[7i..7i+6] = displacement (3), new direction (3) and
+ * the field's step limit at the start.  Device arrays. */
+int gv_unit_field(void *ctx, int type, const double *E, const double *s, const double *dir, long long n,
+                  double *out, void *stream);
 
 int gv_unit_distance(void *ctx, const double *pos, const double *dir, const int *sub,
                      long long n, double *dist, int *next, int *plane, void *stream);

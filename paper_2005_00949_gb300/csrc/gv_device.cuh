@@ -69,6 +69,7 @@ struct GeoConst {
   double wx[2], wy[2];  // the x and y walls {-h, +h}
   float inv_pitch_x, inv_pitch_y;
   int walls_x, walls_y; // 0: unbounded in that direction
+  int field_axis;       // uniform magnetic field along x, y or z
 };
 
 struct CutConst {
@@ -83,6 +84,7 @@ template <typename R> struct RConst {
   R tcut, gcut, ecut, ecut_push;  // ecut_push = max(e- cut, tracking cut)
   R ln_Elo[kNModel], inv_dl[kNModel], cut[kNModel];
   R inv_X0[GV_MAX_MAT];  // 1 / radiation length, 1/cm
+  R field_k;             // 2.99792458 B: curvature (1/cm) times momentum (MeV/c); 0 without field
 };
 
 // Read-only view of everything one step needs.
@@ -364,6 +366,61 @@ __device__ __forceinline__ void rotate_vec(const R d[3], R along, R perp, R cp, 
   }
   const R inv = R(1) / m_sqrt(n2);
   rotate(d, along * inv, perp * inv, cp, sp, o);
+}
+
+// ---------------------------------------------------------------- magnetic field
+// Uniform field along a coordinate axis b (field propagation, Sec. 3.6): a
+// track of charge q and momentum p turns as dd/ds = q k (d x b), k = field_k
+// / p.  With d = a + c0, a = (d.b) b, g = c0 x b and th = q k s, the exact
+// helix moves the track by a s + c0 s sin(th)/th + g s (1 - cos th)/th and
+// turns it to a + c0 cos th + g sin th; both quotients come from sin and cos
+// of th/2, free of cancellation for small th.
+constexpr double kFieldSagitta = 1e-3;  // cm
+constexpr double kFieldMaxTurn = 0.2;   // rad
+
+template <typename R> __device__ __forceinline__ R field_curv(const View<R> &V, int type, R E) {
+  const R p = m_sqrt(E * (E + R(2) * static_cast<R>(kME)));
+  return (type == 2 ? V.rc.field_k : -V.rc.field_k) / p;
+}
+
+// Step limit: chord sagitta <= 10 um and turn <= 0.2 rad of the helix
+// (curvature |k| sin of the angle to the field).
+template <typename R>
+__device__ __forceinline__ R field_limit(const View<R> &V, int type, R E, R u, R v, R w) {
+  if (type == 0 || V.rc.field_k == R(0)) return r_inf<R>();
+  // sin^2 of the angle to the field from the two other components (no
+  // cancellation when the track runs nearly along the field)
+  const int ax = V.geo.field_axis;
+  const R sa2 = ax == 0 ? v * v + w * w : (ax == 1 ? u * u + w * w : u * u + v * v);
+  const R k = field_curv(V, type, E);
+  const R keff = m_sqrt(sa2) * (k < R(0) ? -k : k);
+  if (!(keff > R(0))) return r_inf<R>();
+  const R a = m_sqrt(static_cast<R>(8.0 * kFieldSagitta) / keff), b = static_cast<R>(kFieldMaxTurn) / keff;
+  return a < b ? a : b;
+}
+
+template <typename R>
+__device__ __forceinline__ void helix(const View<R> &V, int type, R E, R s, const R d[3], R dp[3], R nd[3]) {
+  const int ax = V.geo.field_axis;
+  const R db = d[ax];
+  R a[3] = {R(0), R(0), R(0)};
+  a[ax] = db;
+  const R c0[3] = {d[0] - a[0], d[1] - a[1], d[2] - a[2]};
+  // g = c0 x b for b the unit vector of axis ax
+  R g[3];
+  if (ax == 0) { g[0] = R(0); g[1] = c0[2]; g[2] = -c0[1]; }
+  else if (ax == 1) { g[0] = -c0[2]; g[1] = R(0); g[2] = c0[0]; }
+  else { g[0] = c0[1]; g[1] = -c0[0]; g[2] = R(0); }
+  const R th = field_curv(V, type, E) * s;
+  R sh, ch;
+  m_sincos(R(0.5) * th, &sh, &ch);
+  const R sn = R(2) * sh * ch, cs = R(1) - R(2) * sh * sh;
+  const R sc = th != R(0) ? sn / th : R(1), cc = th != R(0) ? R(2) * sh * sh / th : R(0);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    dp[j] = a[j] * s + c0[j] * (s * sc) + g[j] * (s * cc);
+    nd[j] = a[j] + c0[j] * cs + g[j] * sn;
+  }
 }
 
 // ---------------------------------------------------------------- multiple scattering

@@ -121,7 +121,9 @@ __device__ __forceinline__ void set_status(Ctl *ctl, int code) { atomicCAS(&ctl-
 // point and u[] holds the step's eight uniforms for its final state.
 // Secondaries made so far go to `kids`; kk is the step index whose counter
 // blocks derive the children's ids.
-template <typename R>
+// FIELD: compiled with the magnetic-field propagation (a field-free kernel
+// keeps its registers for the rest of the step).
+template <typename R, bool FIELD>
 __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kids<R> &kids, uint32_t &kk,
                           BlockCnt *bc, int &proc_out, R *u, int &lim_out, Pending<R> *pd) {
   kids.n = 0;
@@ -166,6 +168,10 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
     const R Rr = t.type == 1 ? s4.z : s4.w;
     const R a = static_cast<R>(kAlphaR) * Rr, b = Rr < static_cast<R>(kRhoF) ? Rr : static_cast<R>(kRhoF);
     s_cont = a > b ? a : b;
+    if (FIELD && V.rc.field_k != R(0)) {  // the field's step limit acts like the continuous one
+      const R sf = field_limit(V, t.type, t.E, t.u, t.v, t.w);
+      s_cont = sf < s_cont ? sf : s_cont;
+    }
   }
   // GeomQuery
   int next, plane;
@@ -182,17 +188,39 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   // Propagation: FP64 positions, advanced by displacements s d formed in R
   // (s and d are R already; in FP64 mode this is one fused multiply-add)
   double mx = 0.0, my = 0.0;  // step midpoint: only cell scoring reads it
-  if (S->cell) {
-    mx = t.x + static_cast<double>(R(0.5) * s * t.u);
-    my = t.y + static_cast<double>(R(0.5) * s * t.v);
-  }
-  t.x += static_cast<double>(s * t.u);
-  t.y += static_cast<double>(s * t.v);
-  t.z += static_cast<double>(s * t.w);
-  if (lim == 0) {
-    if (plane >= 0) t.z = V.zb[plane];
-    else if (plane == -2) t.x = V.geo.wx[t.u > R(0) ? 1 : 0];
-    else if (plane == -3) t.y = V.geo.wy[t.v > R(0) ? 1 : 0];
+  if (FIELD && charged && V.rc.field_k != R(0)) {  // the helix of the pre-step momentum
+    const R d0[3] = {t.u, t.v, t.w};
+    R dp[3], nd[3];
+    if (S->cell) {
+      helix(V, t.type, t.E, R(0.5) * s, d0, dp, nd);
+      mx = t.x + static_cast<double>(dp[0]);
+      my = t.y + static_cast<double>(dp[1]);
+    }
+    helix(V, t.type, t.E, s, d0, dp, nd);
+    t.x += static_cast<double>(dp[0]);
+    t.y += static_cast<double>(dp[1]);
+    t.z += static_cast<double>(dp[2]);
+    if (lim == 0) {  // the crossed plane, chosen with the pre-step direction
+      if (plane >= 0) t.z = V.zb[plane];
+      else if (plane == -2) t.x = V.geo.wx[t.u > R(0) ? 1 : 0];
+      else if (plane == -3) t.y = V.geo.wy[t.v > R(0) ? 1 : 0];
+    }
+    t.u = nd[0];
+    t.v = nd[1];
+    t.w = nd[2];
+  } else {
+    if (S->cell) {
+      mx = t.x + static_cast<double>(R(0.5) * s * t.u);
+      my = t.y + static_cast<double>(R(0.5) * s * t.v);
+    }
+    t.x += static_cast<double>(s * t.u);
+    t.y += static_cast<double>(s * t.v);
+    t.z += static_cast<double>(s * t.w);
+    if (lim == 0) {
+      if (plane >= 0) t.z = V.zb[plane];
+      else if (plane == -2) t.x = V.geo.wx[t.u > R(0) ? 1 : 0];
+      else if (plane == -3) t.y = V.geo.wy[t.v > R(0) ? 1 : 0];
+    }
   }
   if (Sig > R(0)) t.nlam = (lim == 1) ? R(0) : t.nlam - s * Sig;
   t.step = k + 1;
@@ -527,7 +555,7 @@ template <typename R> __global__ void prim_emax_kernel(const DevState<R> *S) {
 #define GV_STEP_BOUNDS __launch_bounds__(GV_MAX_BLOCK, sizeof(R) == 4 ? GV_MIN_BLOCKS : 2)
 #endif
 
-template <typename R, bool SORT, bool MERGE>
+template <typename R, bool SORT, bool MERGE, bool FIELD>
 __global__ void GV_STEP_BOUNDS
     step_kernel(const DevState<R> *__restrict__ S, int parity) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -692,7 +720,7 @@ __global__ void GV_STEP_BOUNDS
       for (int m = 0; m < inner && alive && proc < 0; ++m) {
         ++n_iter;
         const uint32_t before = t.step;
-        alive = step_track(V, S, t, kids, kstep, &bc, proc, u, lim, pd) != 0;
+        alive = step_track<R, FIELD>(V, S, t, kids, kstep, &bc, proc, u, lim, pd) != 0;
         // NaN energy, or a non-finite z (tested on its exponent bits: an FP64
         // comparison would take the FP64 pipe)
         if (!(t.E == t.E) || (__double2hiint(t.z) & 0x7ff00000) == 0x7ff00000) {
@@ -994,7 +1022,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_ALONG_MIN_BLOCKS : 2)
       for (int m = 0; m < S->along_steps && alive && proc < 0; ++m) {
         ++n_iter;
         const uint32_t before = t.step;
-        alive = step_track(V, S, t, kids, kstep, &bc, proc, u, lim, static_cast<Pending<R> *>(nullptr)) != 0;
+        alive = step_track<R, true>(V, S, t, kids, kstep, &bc, proc, u, lim, static_cast<Pending<R> *>(nullptr)) != 0;
         if (!(t.E == t.E) || (__double2hiint(t.z) & 0x7ff00000) == 0x7ff00000) {
           set_status(ctl, GV_ERR_NUMERIC);
           alive = false;
@@ -1189,6 +1217,7 @@ int validate(const gv_material *mats, int n_mats, const gv_layers *geo, const gv
   for (int j = 0; j < geo->n_sub; ++j)
     if (!(geo->sub_thick_cm[j] > 0) || geo->sub_mat[j] < 0 || geo->sub_mat[j] >= n_mats) return GV_ERR_BAD_ARG;
   if (geo->nx_cells < 0 || geo->ny_cells < 0) return GV_ERR_BAD_ARG;
+  if (!(std::fabs(geo->field_T) < 1e4) || geo->field_axis < 0 || geo->field_axis > 2) return GV_ERR_BAD_ARG;
   if ((geo->nx_cells > 0 || geo->ny_cells > 0) &&
       !(geo->nx_cells > 0 && geo->ny_cells > 0 && geo->half_x_cm > 0 && geo->half_y_cm > 0))
     return GV_ERR_BAD_ARG;
@@ -1332,6 +1361,8 @@ template <typename R> View<R> make_view(const Ctx *c) {
   v.geo.wy[1] = c->geo.half_y_cm;
   v.geo.walls_x = c->geo.half_x_cm > 0.0;
   v.geo.walls_y = c->geo.half_y_cm > 0.0;
+  v.geo.field_axis = c->geo.field_axis;
+  v.rc.field_k = static_cast<R>(2.99792458 * c->geo.field_T);
   v.geo.pitch_x = c->geo.nx_cells > 0 ? 2.0 * c->geo.half_x_cm / c->geo.nx_cells : 1.0;
   v.geo.pitch_y = c->geo.ny_cells > 0 ? 2.0 * c->geo.half_y_cm / c->geo.ny_cells : 1.0;
   v.geo.inv_pitch_x = static_cast<float>(1.0 / v.geo.pitch_x);
@@ -1356,10 +1387,11 @@ template <typename R> View<R> make_view(const Ctx *c) {
 template <typename R> using StepFn = void (*)(const DevState<R> *, int);
 
 // The step kernel compiled for this configuration: basketizer or not, merged
-// or direct scoring.
-template <typename R> StepFn<R> pick_step_kernel(const gv_config &c) {
-  if (c.process_sort) return c.scoring ? step_kernel<R, true, true> : step_kernel<R, true, false>;
-  return c.scoring ? step_kernel<R, false, true> : step_kernel<R, false, false>;
+// or direct scoring, with or without the field propagation.
+template <typename R> StepFn<R> pick_step_kernel(const gv_config &c, bool field) {
+  if (field) return c.process_sort ? step_kernel<R, true, false, true> : step_kernel<R, false, false, true>;
+  if (c.process_sort) return c.scoring ? step_kernel<R, true, true, false> : step_kernel<R, true, false, false>;
+  return c.scoring ? step_kernel<R, false, true, false> : step_kernel<R, false, false, false>;
 }
 
 template <typename R> int prepare_device(Ctx *c) {
@@ -1395,7 +1427,7 @@ template <typename R> int prepare_device(Ctx *c) {
     return GV_OK;
   }
   c->smem_bytes = c->req_off + (c->cfg.process_sort ? sizeof(IReq<R>) * c->cfg.block_size : 0);
-  const void *kern = reinterpret_cast<const void *>(pick_step_kernel<R>(c->cfg));
+  const void *kern = reinterpret_cast<const void *>(pick_step_kernel<R>(c->cfg, c->geo.field_T != 0.0));
   CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(c->smem_bytes)));
   int occ = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, c->cfg.block_size, c->smem_bytes));
@@ -1447,7 +1479,7 @@ template <typename R> int capture_graph(Ctx *c) {
       interact_kernel<R><<<c->grid_b, 256, 0, c->stream>>>(S, i & 1);
     }
   } else {
-    const StepFn<R> step = pick_step_kernel<R>(c->cfg);
+    const StepFn<R> step = pick_step_kernel<R>(c->cfg, c->geo.field_T != 0.0);
     for (int i = 0; i < c->cfg.generations_per_graph; ++i)
       step<<<c->grid, c->cfg.block_size, c->smem_bytes, c->stream>>>(S, i & 1);
   }
@@ -1668,6 +1700,7 @@ int gv_setup(void **ctx_out, const gv_material *mats, int n_mats, const gv_layer
   if (cfg) c = *cfg;
   rc = validate_cfg(c);
   if (rc) return rc;
+  if (geo->field_T != 0.0 && c.scoring != 0) return GV_ERR_BAD_ARG;  // no merged-scoring field kernel
   Ctx *x = new Ctx();
   x->cfg = c;
   x->mats.assign(mats, mats + n_mats);
@@ -1914,6 +1947,7 @@ extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long 
   if (!c || n < 0 || (n > 0 && !prim) || n_events < 1 || !edep || !escape_E || !counters) return GV_ERR_BAD_ARG;
   if (!c->tables) return GV_ERR_NO_TABLES;
   if (c->cfg.precision != GV_MIXED) return GV_ERR_BAD_ARG;  // the array is sized for the mixed layout
+  if (c->geo.field_T != 0.0) return GV_ERR_BAD_ARG;          // its kernel is the field-free one
   if (n_events > kStaticMaxEvents || n > 0xffffffffll) return GV_ERR_BAD_ARG;
   if ((n > 0 && !is_device_ptr(prim)) || !is_device_ptr(edep) || !is_device_ptr(escape_E)) return GV_ERR_BAD_ARG;
   if (cudaSetDevice(c->device) != cudaSuccess) return GV_ERR_CUDA;
@@ -1922,11 +1956,11 @@ extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long 
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t smem = c->req_off;  // tables and geometry; the non-basketizing kernel
-  if (cudaFuncSetAttribute(step_kernel<float, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(step_kernel<float, false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess)
     return GV_ERR_CUDA;
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_kernel<float, false, false>, c->cfg.block_size, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_kernel<float, false, false, false>, c->cfg.block_size, smem) !=
           cudaSuccess ||
       occ < 1)
     return GV_ERR_CUDA;
@@ -1965,7 +1999,7 @@ extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long 
   int between = 1;
   for (;;) {
     for (int i = 0; i < 2 * between; ++i)
-      step_kernel<float, false, false><<<grid, c->cfg.block_size, smem, st>>>(S, i & 1);
+      step_kernel<float, false, false, false><<<grid, c->cfg.block_size, smem, st>>>(S, i & 1);
     if (cudaGetLastError() != cudaSuccess) return GV_ERR_CUDA;
     if (cudaMemcpyAsync(c->h_ctl, s.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)

@@ -130,6 +130,22 @@ __global__ void k_msc(View<R> V, const int *sub, const double *Ea, const double 
   op[3 * i + 2] = z;
 }
 
+template <typename R>
+__global__ void k_field(View<R> V, int type, const double *E, const double *sv, const double *dir, long long n,
+                        double *out) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const R d[3] = {static_cast<R>(dir[3 * i]), static_cast<R>(dir[3 * i + 1]), static_cast<R>(dir[3 * i + 2])};
+  R dp[3], nd[3];
+  const R e = static_cast<R>(E[i]);
+  helix(V, type, e, static_cast<R>(sv[i]), d, dp, nd);
+  for (int j = 0; j < 3; ++j) {
+    out[7 * i + j] = dp[j];
+    out[7 * i + 3 + j] = nd[j];
+  }
+  out[7 * i + 6] = field_limit(V, type, e, d[0], d[1], d[2]);
+}
+
 int launch_status() { return cudaGetLastError() == cudaSuccess ? GV_OK : GV_ERR_CUDA; }
 
 }  // namespace
@@ -208,6 +224,14 @@ int gv_unit_msc(void *ctx, const int *sub, const double *E_pre, const double *E_
   GV_UNIT_DISPATCH(
       (k_msc<float><<<blocks_for(n), kThreads, 0, s>>>(vf, sub, E_pre, E_post, sv, dir, pos, u, n, out_dir, out_pos)),
       (k_msc<double><<<blocks_for(n), kThreads, 0, s>>>(vd, sub, E_pre, E_post, sv, dir, pos, u, n, out_dir, out_pos)))
+}
+
+int gv_unit_field(void *ctx, int type, const double *E, const double *sv, const double *dir, long long n,
+                  double *out, void *stream) {
+  if (!ctx || type < 1 || type > 2 || n < 0 || (n > 0 && (!E || !sv || !dir || !out))) return GV_ERR_BAD_ARG;
+  if (n == 0) return GV_OK;
+  GV_UNIT_DISPATCH((k_field<float><<<blocks_for(n), kThreads, 0, s>>>(vf, type, E, sv, dir, n, out)),
+                   (k_field<double><<<blocks_for(n), kThreads, 0, s>>>(vd, type, E, sv, dir, n, out)))
 }
 
 }  // extern "C"

@@ -41,7 +41,8 @@ class gv_material(C.Structure):
 class gv_layers(C.Structure):
     _fields_ = [("n_layers", C.c_int), ("n_sub", C.c_int), ("sub_thick_cm", C.c_double * 8),
                 ("sub_mat", C.c_int * 8), ("half_x_cm", C.c_double), ("half_y_cm", C.c_double),
-                ("nx_cells", C.c_int), ("ny_cells", C.c_int)]
+                ("nx_cells", C.c_int), ("ny_cells", C.c_int), ("field_T", C.c_double),
+                ("field_axis", C.c_int)]
 
 
 class gv_cuts(C.Structure):
@@ -97,6 +98,7 @@ def load():
             lib.gv_unit_interact.argtypes = [vp, i, i, vp, vp, vp, ll, vp, vp, vp]
             lib.gv_unit_distance.argtypes = [vp, vp, vp, vp, ll, vp, vp, vp, vp]
             lib.gv_unit_msc.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, ll, vp, vp, vp]
+            lib.gv_unit_field.argtypes = [vp, i, vp, vp, vp, ll, vp, vp]
             _lib = lib
     return _lib
 
@@ -148,6 +150,7 @@ class Context:
             geo.sub_thick_cm[j] = t
             geo.sub_mat[j] = wl.sub_mat[j]
         geo.half_x_cm, geo.half_y_cm, geo.nx_cells, geo.ny_cells = wl.half_x, wl.half_y, wl.nx, wl.ny
+        geo.field_T, geo.field_axis = wl.field_T, wl.field_axis
         cuts = gv_cuts(wl.gamma_cut, wl.e_cut, wl.track_cut, wl.process_mask)
         cfg = config if config is not None else gv_default_config()
         for k, v in overrides.items():
@@ -245,6 +248,11 @@ class Context:
         _check(self.lib.gv_unit_msc(self.h, _ptr(sub), _ptr(E_pre), _ptr(E_post), _ptr(s), _ptr(d), _ptr(pos),
                                     _ptr(u), sub.numel(), _ptr(out_dir), _ptr(out_pos), _stream_ptr(stream)),
                "gv_unit_msc")
+
+
+    def gv_unit_field(self, ptype, E, s, d, out, stream=None):
+        _check(self.lib.gv_unit_field(self.h, ptype, _ptr(E), _ptr(s), _ptr(d), E.numel(), _ptr(out),
+                                      _stream_ptr(stream)), "gv_unit_field")
 
 
 def gv_unit_philox(ctr, key, out, stream=None):

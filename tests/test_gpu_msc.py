@@ -1,4 +1,5 @@
-"""Showers with multiple scattering (GV_P_MSC) against the oracle.
+"""Showers with multiple scattering (GV_P_MSC) and in a magnetic field
+against the oracle.
 
 The scattering draws its uniforms from counter block 2 of each step on both
 sides, so FP64 histories coincide with the oracle's event by event, and the
@@ -75,3 +76,32 @@ def test_msc_testem3_and_bench_workload_measured(gvmod, oracle_mod):
     _report("config4_msc", events=wl4.n_events, kernel_ms=r4["kernel_ms"],
             events_per_s=wl4.n_events / (r4["kernel_ms"] / 1e3), steps_per_s=c["steps"] / (r4["kernel_ms"] / 1e3),
             steps=c["steps"], layers=_layer_stats(wl4, r4["edep"], ref4["edep"]))
+
+
+# ---------------------------------------------------------------- magnetic field
+def test_fp64_field_showers_follow_oracle_event_by_event(gvmod, oracle_mod):
+    wl = W.with_field(W.pblar_testem3(300, 1000.0), 4.0, 1)
+    r = _run(gvmod, wl, precision=1, per_event_counts=1)
+    ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
+    same = np.all(r["counts"][:, :11] == ref["counts"][:, :11], axis=1)
+    assert same.mean() >= 0.9, same.mean()
+    assert np.abs(r["edep"][same] - ref["edep"][same]).max() < 1e-9 * 1000.0
+
+
+def test_testem3_field_and_msc_paper_conditions(gvmod, oracle_mod):
+    """The paper's TestEm3 conditions as far as this physics list goes: 50 x
+    (2.3 mm Pb + 5.7 mm LAr), 10 GeV e-, 4 T transverse field, multiple
+    scattering.  Parity with the oracle (mixed precision), conservation, and
+    the per-material deposits and counts next to the paper's tables."""
+    wl = W.with_msc(W.with_field(W.pblar_testem3(1000, 10_000.0), 4.0, 1))
+    r = _run(gvmod, wl, per_event_counts=1)
+    ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
+    layer_parity(wl, r["edep"], ref["edep"])
+    assert np.abs(_conservation(wl, r)).max() < 1e-5
+    mat = r["edep"].reshape(wl.n_events, 50, 2).sum(1).mean(0)
+    cnt = r["counts"].mean(0)
+    _report("testem3_PbLAr_10GeV_4T_msc", events=wl.n_events, kernel_ms=r["kernel_ms"],
+            edep_Pb_GeV=float(mat[0] / 1e3), edep_LAr_GeV=float(mat[1] / 1e3),
+            gammas=float(cnt[4]), electrons=float(cnt[5] - 1), positrons=float(cnt[6]),
+            charged_steps=float(cnt[2] + cnt[3]), neutral_steps=float(cnt[1]),
+            layers=_layer_stats(wl, r["edep"], ref["edep"]))

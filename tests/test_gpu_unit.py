@@ -303,3 +303,49 @@ def test_msc_matches_oracle(torch, ctx, oracle_pbps):
         assert np.abs(off_g - off_o).max() <= tol * max(np.abs(off_o).max(), 0.05), (i, off_g, off_o)
         # the end point stays in its sub-slab and the box
         assert zb[sub[i]] <= gp[i][2] <= zb[sub[i] + 1] and np.abs(gp[i][:2]).max() <= 20.0
+
+
+# ---------------------------------------------------------------- magnetic field
+@pytest.fixture(scope="module", params=[0, 1], ids=["mixed", "fp64"])
+def fctx(request, gvmod):
+    wl = W.with_field(W.pbps_electrons(1), 4.0, 1)
+    c = gvmod.Context(wl, gvmod.gv_default_config(precision=request.param, stack_capacity=1 << 12))
+    c.prec = request.param
+    c.wl = wl
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("ptype", [1, 2])
+def test_helix_matches_oracle(torch, fctx, oracle_mod, ptype):
+    o = oracle_mod.Oracle(fctx.wl)
+    rng = np.random.default_rng(80 + ptype)
+    E = 10.0 ** rng.uniform(-3, 5, N)
+    c = rng.uniform(-1, 1, N)
+    ph = rng.uniform(0, 2 * math.pi, N)
+    d = np.stack([np.sqrt(1 - c * c) * np.cos(ph), np.sqrt(1 - c * c) * np.sin(ph), c], 1)
+    d[:20] = [0, 1, 0]  # along the field
+    # path lengths up to 0.2 cm (many turns at low energy), and up to the
+    # field's own step limit on every 37th track
+    lim = np.array([o.field_step_limit(ptype, E[i], d[i]) for i in range(0, N, 37)])
+    s = rng.uniform(0, 1, N) * 0.2
+    s[::37] = np.minimum(lim, 10.0) * rng.uniform(0, 1, len(lim))
+    out = torch.zeros((N, 7), dtype=torch.float64, device="cuda")
+    fctx.gv_unit_field(ptype, _dev(torch, E), _dev(torch, s), _dev(torch, d), out)
+    g = out.cpu().numpy()
+    tol = TOL[fctx.prec]
+    sel = np.concatenate([np.arange(40), np.arange(0, N, 37)[:3000],
+                          np.random.default_rng(9).choice(N, 6000, False)])
+    for i in sel:
+        dp, nd = o.helix(ptype, E[i], s[i], d[i])
+        sl = o.field_step_limit(ptype, E[i], d[i])
+        assert np.abs(g[i, :3] - dp).max() <= tol * max(s[i], 0.05), (i, g[i, :3], dp)
+        assert np.abs(g[i, 3:6] - nd).max() <= tol, (i, g[i, 3:6], nd)
+        if math.isinf(sl):
+            assert math.isinf(g[i, 6])
+        else:
+            # sin^2 of the angle to the field carries the direction's own
+            # rounding (~1e-7 in R = FP32) relative to sin^2 itself
+            sa2 = 1.0 - d[i][1] ** 2
+            cond = max(1.0, (1e-7 if fctx.prec == 0 else 1e-15) / max(sa2, 1e-300) / tol)
+            assert abs(g[i, 6] - sl) <= tol * sl * cond, (i, g[i, 6], sl, sa2)

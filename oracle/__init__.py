@@ -9,6 +9,7 @@ no transport arithmetic.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -50,7 +51,8 @@ class OrSetup(C.Structure):
                 ("n_sub", C.c_int), ("sub_thick", C.c_double * 8), ("sub_mat", C.c_int * 8),
                 ("half_x", C.c_double), ("half_y", C.c_double), ("nx", C.c_int), ("ny", C.c_int),
                 ("gamma_cut", C.c_double), ("e_cut", C.c_double), ("track_cut", C.c_double),
-                ("process_mask", C.c_uint), ("field_T", C.c_double), ("field_axis", C.c_int)]
+                ("process_mask", C.c_uint), ("field_T", C.c_double), ("field_axis", C.c_int),
+                ("reject_min", C.c_double * 6)]
 
 
 def _load():
@@ -97,7 +99,10 @@ def _load():
             lib.or_locate.argtypes = [p, d, d]
             lib.or_distance.restype = d
             lib.or_distance.argtypes = [p, p, p, i, C.POINTER(i), C.POINTER(i)]
-            lib.or_interact.argtypes = [p, i, i, d, p, p, p]
+            lib.or_interact.argtypes = [p, i, i, d, p, p, p, p]
+            lib.or_has_rejection.argtypes = [i]
+            lib.or_reject_sample.restype = d
+            lib.or_reject_sample.argtypes = [p, i, d, p, C.POINTER(d), C.POINTER(i)]
             lib.or_safety.restype = d
             lib.or_safety.argtypes = [p, p, i]
             lib.or_msc_theta0.restype = d
@@ -154,6 +159,8 @@ class Oracle:
         s.gamma_cut, s.e_cut, s.track_cut = wl.gamma_cut, wl.e_cut, wl.track_cut
         s.process_mask = wl.process_mask
         s.field_T, s.field_axis = wl.field_T, wl.field_axis
+        for m in range(6):
+            s.reject_min[m] = wl.reject_min[m] if wl.reject_min is not None else math.inf
         self._setup = s
         h = C.c_void_p()
         rc = lib.or_create(C.byref(s), C.byref(h))
@@ -238,12 +245,26 @@ class Oracle:
             xi[i] = x.value
         return out, xi
 
-    def interact(self, ptype: int, proc: int, E: float, d, u) -> tuple:
+    def interact(self, ptype: int, proc: int, E: float, d, u, rng=(0, 0, 0, 0, 0)) -> tuple:
+        """rng: (id_lo, id_hi, step, key0, key1) of the interacting step (the
+        rejection samplers' stream)."""
         dd = np.ascontiguousarray(d, dtype=np.float64)
         uu = np.ascontiguousarray(u, dtype=np.float64)
+        rr = np.ascontiguousarray(rng, dtype=np.uint32)
         out = np.zeros(24)
-        r = self.lib.or_interact(self.h, ptype, proc, E, _ptr(dd), _ptr(uu), _ptr(out))
+        r = self.lib.or_interact(self.h, ptype, proc, E, _ptr(dd), _ptr(uu), _ptr(rr), _ptr(out))
         return r, out
+
+    @staticmethod
+    def has_rejection(model: int) -> bool:
+        return bool(_load().or_has_rejection(model))
+
+    def reject_sample(self, model: int, E: float, rng) -> tuple:
+        """(physical variable, reduced variable, trials) by rejection."""
+        rr = np.ascontiguousarray(rng, dtype=np.uint32)
+        xi, tr = C.c_double(), C.c_int()
+        v = self.lib.or_reject_sample(self.h, model, E, _ptr(rr), C.byref(xi), C.byref(tr))
+        return v, xi.value, tr.value
 
     # -- geometry
     def n_subtotal(self) -> int:

@@ -520,6 +520,70 @@ int or_alias_table(const or_ctx *c, int model, int ie, double *pdf, float *q, in
   return 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* rejection samplers (the "rejection" method of Sec. 3.5)             */
+/* ------------------------------------------------------------------ */
+/* A proposal from a density with a closed-form inverse, accepted with the
+ * ratio of the DCS to a bound of it (Sec. 3.5 compares this with sampling
+ * tables and chooses per energy range).  Trial j takes its proposal and
+ * acceptance uniforms from counter block REJ_BLOCK0 + j/2 of the
+ * interacting step (words 2(j%2) and 2(j%2)+1); after REJ_MAX_TRIALS
+ * rejections the last proposal stands.  Built for:
+ *   pair       x uniform on [m/k, 1 - m/k]; accept 1 - 4/3 x(1-x)  (<= 1)
+ *   brems      k = k_c (T/k_c)^xi (density 1/k); accept
+ *              (4/3 - 4/3 y + y^2) / (4/3), y = k/(T+m)
+ *   Compton    eps = eps0^(1-xi) (density 1/eps); accept
+ *              (1 + eps^2 - eps sin^2 theta) / 2
+ * The proposal's xi is the reduced variable of the sampling tables. */
+/* uniform in (0, 1] from a 32-bit Philox word: 24 bits, exact in FP32 and FP64 */
+static double u24(uint32_t x) { return (double)((x >> 8) + 1u) * (1.0 / 16777216.0); }
+
+#define REJ_BLOCK0 3u
+#define REJ_MAX_TRIALS 64
+
+int or_has_rejection(int model) {
+  return model == OR_M_PAIR || model == OR_M_BREM || model == OR_M_COMPTON;
+}
+
+double or_reject_sample(const or_ctx *c, int model, double E, const uint32_t rng[5], double *xi_out,
+                        int *trials) {
+  const double cut = model_cut(c, model);
+  double v = 0.0, xi = 0.0;
+  int j = 0;
+  uint32_t w[4] = {0, 0, 0, 0};
+  for (j = 0; j < REJ_MAX_TRIALS; ++j) {
+    if ((j & 1) == 0) {
+      const uint32_t ctr[4] = {rng[0], rng[1], rng[2], REJ_BLOCK0 + (uint32_t)(j >> 1)};
+      const uint32_t key[2] = {rng[3], rng[4]};
+      or_philox4x32_10(ctr, key, w);
+    }
+    xi = u24(w[2 * (j & 1)]);
+    const double ua = u24(w[2 * (j & 1) + 1]);
+    double f = 0.0;
+    v = xi_to_var(model, E, xi, cut);
+    if (model == OR_M_PAIR) {
+      f = 1.0 - 4.0 / 3.0 * v * (1.0 - v);
+    } else if (model == OR_M_BREM) {
+      const double y = v / (E + ME);
+      f = (4.0 / 3.0 - 4.0 / 3.0 * y + y * y) * 0.75;
+    } else {
+      const double K = E / ME, t = (1.0 - v) / (K * v), s2 = t * (2.0 - t);
+      f = 0.5 * (1.0 + v * v - v * s2);
+    }
+    if (ua <= f) break;
+  }
+  if (trials) *trials = j < REJ_MAX_TRIALS ? j + 1 : REJ_MAX_TRIALS;
+  if (xi_out) *xi_out = xi;
+  return v;
+}
+
+/* The sampler the setup chooses for (model, E): rejection where it is built
+ * and E >= reject_min[model], else the sampling tables (u3: their uniforms). */
+static double sample_var(const or_ctx *c, int model, double E, const double *u3, const uint32_t rng[5]) {
+  if (or_has_rejection(model) && E >= c->s.reject_min[model]) return or_reject_sample(c, model, E, rng, NULL, NULL);
+  return or_alias_sample(c, model, E, u3, NULL);
+}
+
 /* Sample the physical variable at energy E with uniforms
  * u[0]: grid-energy choice, u[1]: bin + alias, u[2]: position in the bin. */
 double or_alias_sample(const or_ctx *c, int model, double E, const double *u, double *xi_out) {
@@ -562,9 +626,6 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
   }
   out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
-
-/* uniform in (0,1] from the top 24 bits */
-static double u24(uint32_t x) { return (double)((x >> 8) + 1u) * (1.0 / 16777216.0); }
 
 /* ------------------------------------------------------------------ */
 /* tables                                                              */
@@ -915,7 +976,7 @@ static void annihilate_at_rest(kids_t *k, double u6, double u7) {
  * Returns: 1 primary survives, 0 primary died, -1 no interaction possible.
  * *local: energy deposited at the interaction point. */
 static int interact(const or_ctx *c, int type, int p, double *E, double dir[3], const double *u,
-                    kids_t *kids, double *local, int *n_pair, int *n_annih) {
+                    const uint32_t rng[5], kids_t *kids, double *local, int *n_pair, int *n_annih) {
   const or_setup *s = &c->s;
   double ecut_push = fmax(s->e_cut, s->track_cut);
   double ua[3] = {u[2], u[3], u[4]};
@@ -925,7 +986,7 @@ static int interact(const or_ctx *c, int type, int p, double *E, double dir[3], 
   if (type == OR_GAMMA) {
     double k = *E;
     if (p == 0) { /* Compton */
-      double eps = or_alias_sample(c, OR_M_COMPTON, k, ua, NULL);
+      double eps = sample_var(c, OR_M_COMPTON, k, ua, rng);
       double K = k / ME, ct = 1.0 - (1.0 - eps) / (K * eps);
       if (ct < -1.0) ct = -1.0;
       if (ct > 1.0) ct = 1.0;
@@ -950,7 +1011,7 @@ static int interact(const or_ctx *c, int type, int p, double *E, double dir[3], 
     }
     /* pair */
     if (k <= 2.0 * ME) return -1;
-    double x = or_alias_sample(c, OR_M_PAIR, k, ua, NULL);
+    double x = sample_var(c, OR_M_PAIR, k, ua, rng);
     double Tm = x * k - ME, Tp = (1.0 - x) * k - ME;
     if (Tm < 0.0) Tm = 0.0;
     if (Tp < 0.0) Tp = 0.0;
@@ -973,7 +1034,7 @@ static int interact(const or_ctx *c, int type, int p, double *E, double dir[3], 
   double T = *E;
   if (p == 0) { /* bremsstrahlung */
     if (T <= s->gamma_cut) return -1;
-    double kg = or_alias_sample(c, OR_M_BREM, T, ua, NULL);
+    double kg = sample_var(c, OR_M_BREM, T, ua, rng);
     double dg[3];
     rotate(dir, cos(ME / (T + ME)), phi, dg);
     if (kg >= s->track_cut) add_kid(kids, OR_GAMMA, kg, dg);
@@ -1025,11 +1086,11 @@ static int interact(const or_ctx *c, int type, int p, double *E, double dir[3], 
 }
 
 int or_interact(const or_ctx *c, int type, int proc, double E, const double dir[3],
-                const double u[8], double *out) {
+                const double u[8], const uint32_t rng[5], double *out) {
   kids_t kids;
   double d[3] = {dir[0], dir[1], dir[2]}, local = 0.0, e = E;
   int np = 0, na = 0;
-  int r = interact(c, type, proc, &e, d, u, &kids, &local, &np, &na);
+  int r = interact(c, type, proc, &e, d, u, rng, &kids, &local, &np, &na);
   for (int i = 0; i < 24; ++i) out[i] = 0.0;
   out[0] = (r == 1) ? e : (r == 0 ? -1.0 : E);
   out[1] = d[0]; out[2] = d[1]; out[3] = d[2];
@@ -1286,7 +1347,8 @@ static void run_event(const job_t *J, long ev, ostack *st) {
       kids_t kids;
       double local = 0.0;
       int npair = 0, nann = 0;
-      int r = interact(c, t.type, proc, &t.E, t.dir, u, &kids, &local, &npair, &nann);
+      const uint32_t rng[5] = {(uint32_t)t.id, (uint32_t)(t.id >> 32), k, key[0], key[1]};
+      int r = interact(c, t.type, proc, &t.E, t.dir, u, rng, &kids, &local, &npair, &nann);
       if (r < 0) continue;
       t.interacted = 1;
       cnt[OR_C_PAIR] += npair;

@@ -83,6 +83,8 @@ typedef struct {
   unsigned process_mask;
   double field_T;                   /* uniform magnetic field, tesla (0: none) */
   int field_axis;                   /* its direction: 0 x, 1 y, 2 z */
+  double reject_min[6];             /* per model: rejection sampling at E >= this (MeV);
+                                       sampling tables below (and for models without one) */
 } or_setup;
 
 typedef struct {
@@ -122,6 +124,12 @@ int or_alias_info(const or_ctx *c, int model, double *E_lo, int *n_E);
 int or_alias_table(const or_ctx *c, int model, int ie, double *pdf, float *q, int *alias);
 double or_alias_sample(const or_ctx *c, int model, double E, const double *u3, double *xi);
 
+/* --- rejection samplers (pair, brems, Compton); rng = {id_lo, id_hi, step,
+ *     key0, key1} of the interacting step, trial j uses counter block 3 + j/2 */
+int or_has_rejection(int model);
+double or_reject_sample(const or_ctx *c, int model, double E, const uint32_t rng[5], double *xi,
+                        int *trials);
+
 /* --- RNG -------------------------------------------------------------- */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
@@ -145,7 +153,7 @@ int or_msc(const or_ctx *c, int sub, double E_pre, double E_post, double s, cons
 
 /* --- interactions given uniforms (unit level) ------------------------ */
 int or_interact(const or_ctx *c, int type, int proc, double E, const double dir[3],
-                const double u[8], double *out /* 16 doubles */);
+                const double u[8], const uint32_t rng[5], double *out /* 24 doubles */);
 
 /* --- full transport --------------------------------------------------- */
 int or_transport(const or_ctx *c, const or_primary *p, long n_prim, long n_events,

@@ -13,7 +13,8 @@ mass fractions, density and mean excitation energy (ICRU 37 / NIST values).
 from __future__ import annotations
 
 import dataclasses
-from typing import List, Sequence
+import math
+from typing import List, Optional, Sequence
 
 import numpy as np
 
@@ -64,6 +65,9 @@ class Workload:
     seed: int = DEFAULT_SEED
     field_T: float = 0.0  # uniform magnetic field (tesla) along field_axis (0 x, 1 y, 2 z)
     field_axis: int = 1
+    # per final-state model (Compton, pair, brems, Moller, Bhabha, annihilation):
+    # rejection sampling at E >= this (MeV) where built, sampling tables below
+    reject_min: Optional[Sequence[float]] = None
 
     @property
     def n_sub(self) -> int:
@@ -173,6 +177,12 @@ def with_field(wl: Workload, tesla: float = 4.0, axis: int = 1) -> Workload:
     """The same workload in a uniform magnetic field (default: 4 T along y,
     transverse to the beam, as in the paper's TestEm3 set-up)."""
     return dataclasses.replace(wl, field_T=tesla, field_axis=axis, name=f"{wl.name}_B{tesla:g}T{'xyz'[axis]}")
+
+
+def with_rejection(wl: Workload, reject_min=(0.0, 0.0, 0.0, math.inf, math.inf, math.inf)) -> Workload:
+    """The same workload sampling Compton, pair and bremsstrahlung final states
+    by rejection above the given energies (MeV), instead of sampling tables."""
+    return dataclasses.replace(wl, reject_min=tuple(reject_min), name=wl.name + "_rej")
 
 
 def with_msc(wl: Workload) -> Workload:

@@ -659,3 +659,82 @@ def test_transport_in_field_conserves_energy_and_charge(oracle_mod):
     # the field bends charged tracks: more steps than without it
     plain = oracle_mod.Oracle(W.with_msc(W.pblar_testem3(20, 2000.0))).transport(n_threads=4)
     assert c[:, 0].sum() > plain["counts"][:, 0].sum()
+
+
+# ---------------------------------------------------------------- rejection samplers
+# The rejection samplers draw from the same DCS shapes as the sampling tables;
+# pinned the same way (chi-square against bin integrals of the DCS), plus the
+# acceptance bound (the ratio never exceeds 1 on a dense grid, so the
+# samplers are unbiased) and the mean trial count against the acceptance
+# probability computed by quadrature.
+@pytest.mark.parametrize("model,E", [(W_M.PAIR, 5.0), (W_M.PAIR, 1e4), (W_M.BREM, 50.0), (W_M.BREM, 1e5),
+                                     (W_M.COMPTON, 0.1), (W_M.COMPTON, 100.0)])
+def test_rejection_sampler_matches_dcs(oracle_mod, model, E):
+    o = oracle_mod.Oracle(W.pbps_electrons(1))
+    assert o.has_rejection(model)
+    n = 40_000
+    vs, xis, tr = np.empty(n), np.empty(n), np.empty(n)
+    for i in range(n):
+        vs[i], xis[i], tr[i] = o.reject_sample(model, E, (i, 7, 3, 0x1234, 0x9876))
+    cut = 1.0 if model == W_M.BREM else 0.0  # the gamma cut of this workload
+    lo = {W_M.PAIR: ME / E, W_M.BREM: cut, W_M.COMPTON: 1 / (1 + 2 * E / ME)}[model]
+    hi = {W_M.PAIR: 1 - ME / E, W_M.BREM: E, W_M.COMPTON: 1.0}[model]
+    # bins equal in the reduced variable (linear for pair, log otherwise)
+    if model == W_M.PAIR:
+        edges = np.linspace(lo, hi, 41)
+    else:
+        edges = np.exp(np.linspace(math.log(lo), math.log(hi), 41))
+    want = np.array([integrate.quad(lambda v: oracle_mod.Oracle.dcs(model, E, v, cut), a, b)[0]
+                     for a, b in zip(edges[:-1], edges[1:])])
+    want = want / want.sum() * n
+    got = np.histogram(vs, edges)[0]
+    chi2 = ((got - want) ** 2 / want).sum()
+    assert stats.chi2.sf(chi2, 39) > 1e-3, chi2
+    # mean trials = 1 / acceptance probability (bound M: 1 pair, 4/3 brems, 2 Compton)
+    M = {W_M.PAIR: 1.0, W_M.BREM: 4.0 / 3.0, W_M.COMPTON: 2.0}[model]
+    if model == W_M.PAIR:
+        acc = integrate.quad(lambda x: oracle_mod.Oracle.dcs(model, E, x, cut), lo, hi)[0] / (hi - lo) / M
+    else:  # proposal density 1/v on [lo, hi]: acceptance = E_prop[v dcs(v)] / M
+        L = math.log(hi / lo)
+        acc = integrate.quad(lambda l: math.exp(l) * oracle_mod.Oracle.dcs(model, E, math.exp(l), cut),
+                             math.log(lo), math.log(hi))[0] / L / M
+    assert abs(tr.mean() * acc - 1.0) < 5 * math.sqrt((1 - acc) / acc / n) * acc + 1e-3, (tr.mean(), 1 / acc)
+
+
+def test_rejection_acceptance_ratio_is_bounded(oracle_mod):
+    """The acceptance ratio (DCS in the proposal's variable over its bound)
+    stays within [0, 1] over the whole range, at energies across the grid."""
+    Oc = oracle_mod.Oracle
+    for E in 10.0 ** np.linspace(-2.9, 6, 40):
+        x = np.linspace(0, 1, 2001)
+        if E > 2 * ME * 1.001:  # pair, linear proposal, bound 1
+            x0 = ME / E
+            v = x0 + x * (1 - 2 * x0)
+            r = np.array([Oc.dcs(W_M.PAIR, E, vv, 0) for vv in v])
+            assert r.max() <= 1.0 + 1e-12 and r.min() >= 0.0
+        if E > 1.0:  # brems above a 1 MeV cut, density 1/k, bound 4/3
+            k = 1.0 * np.exp(x * math.log(E / 1.0))
+            r = np.array([kk * Oc.dcs(W_M.BREM, E, kk, 1.0) for kk in k]) / (4 / 3)
+            assert r.max() <= 1.0 + 1e-12 and r.min() >= 0.0
+        e0 = 1 / (1 + 2 * E / ME)  # Compton, density 1/eps, bound 2
+        e = np.exp((1 - x) * math.log(e0))
+        r = np.array([ee * Oc.dcs(W_M.COMPTON, E, ee, 0) for ee in e]) / 2
+        assert r.max() <= 1.0 + 1e-12 and r.min() >= -1e-12
+
+
+def test_showers_agree_between_samplers(oracle_mod):
+    """Sampling tables and rejection draw from the same DCS: the showers'
+    per-layer means agree within their statistics (different random words,
+    so the comparison is between independent samples)."""
+    wl = W.pbps_electrons(3000, 2000.0)
+    a = oracle_mod.Oracle(wl).transport(n_threads=4)
+    b = oracle_mod.Oracle(W.with_rejection(wl)).transport(n_threads=4)
+    ga = a["edep"].reshape(3000, 50, 2).sum(2)
+    gb = b["edep"].reshape(3000, 50, 2).sum(2)
+    comb = np.sqrt(ga.var(0, ddof=1) / 3000 + gb.var(0, ddof=1) / 3000)
+    pull = np.abs(ga.mean(0) - gb.mean(0))[comb > 0] / comb[comb > 0]
+    assert pull.max() < 4.0, pull.max()
+    c = b["counts"]
+    res = (b["edep"].sum(1) + b["escape"] - (2000.0 + 2 * ME * (c[:, 8] - c[:, 7]))) / 2000.0
+    assert np.abs(res).max() < 1e-9
+    assert not np.array_equal(a["counts"], c)  # the samplers did differ

@@ -100,11 +100,24 @@ typedef struct {
  * discrete parts, e_cut splits ionisation and decides whether Compton,
  * photo- and pair-produced leptons are tracked; track_cut (>= 1 keV) ends
  * tracks.  process_mask: GV_P_* bits of the enabled discrete processes, plus
- * GV_P_MSC for multiple scattering along charged steps. */
+ * GV_P_MSC for multiple scattering along charged steps.  reject_min_MeV[m]:
+ * the final state of model m (GV_M_*) is sampled by rejection at energies
+ * >= this, by sampling tables below (rejection is built for Compton, pair and
+ * bremsstrahlung; a huge value keeps the tables everywhere).  Rejection trial
+ * j draws from counter block 3 + j/2 of the interacting step. */
 typedef struct {
   double gamma_cut_MeV, e_cut_MeV, track_cut_MeV;
   unsigned process_mask;
+  double reject_min_MeV[6];
 } gv_cuts;
+
+/* final-state models (index of gv_cuts.reject_min_MeV and gv_unit_sample) */
+#define GV_M_COMPTON 0
+#define GV_M_PAIR 1
+#define GV_M_BREM 2
+#define GV_M_MOLLER 3
+#define GV_M_BHABHA 4
+#define GV_M_ANNIH 5
 
 /* Launch and memory configuration; gv_default_config fills every field. */
 typedef struct {
@@ -287,6 +300,14 @@ int gv_unit_msc(void *ctx, const int *sub, const double *E_pre, const double *E_
  * the field's step limit at the start.  Device arrays. */
 int gv_unit_field(void *ctx, int type, const double *E, const double *s, const double *dir, long long n,
                   double *out, void *stream);
+
+/* The reduced-variable sampler of model `model` at energies E[i]: method 0
+ * sampling tables (uniforms from counter block 0 of (i, 0, 0) under key
+ * (seed, seed >> 32)), method 1 rejection (block 3 + j/2 for trial j, same
+ * stream; Compton, pair and bremsstrahlung only).  out[3i..3i+2] = physical
+ * variable, reduced variable, trials (1 for the tables). */
+int gv_unit_sample(void *ctx, int model, int method, const double *E, long long n, unsigned long long seed,
+                   double *out, void *stream);
 
 int gv_unit_distance(void *ctx, const double *pos, const double *dir, const int *sub,
                      long long n, double *dist, int *next, int *plane, void *stream);

@@ -49,6 +49,10 @@ __device__ __forceinline__ float log1p_small(float x) {
   return p * x;
 }
 
+template <typename R> __host__ __device__ inline R r_inf_host() {
+  return static_cast<R>(1e300) * static_cast<R>(1e300);  // +inf in R
+}
+
 template <typename R> __device__ __forceinline__ R r_inf();
 template <> __device__ __forceinline__ float r_inf<float>() { return __int_as_float(0x7f800000); }
 template <> __device__ __forceinline__ double r_inf<double>() { return __longlong_as_double(0x7ff0000000000000ll); }
@@ -85,6 +89,7 @@ template <typename R> struct RConst {
   R ln_Elo[kNModel], inv_dl[kNModel], cut[kNModel];
   R inv_X0[GV_MAX_MAT];  // 1 / radiation length, 1/cm
   R field_k;             // 2.99792458 B: curvature (1/cm) times momentum (MeV/c); 0 without field
+  R rej_min[kNModel];    // rejection sampling of model m at E >= rej_min[m]
 };
 
 // Read-only view of everything one step needs.
@@ -242,6 +247,52 @@ template <typename R> __device__ __forceinline__ R reduced_to_physical(int m, R 
       return lo * m_exp(xi * m_log(R(0.5) / lo));
     }
   }
+}
+
+// ---------------------------------------------------------------- rejection
+// The random stream of an interacting step: counter (id_lo, id_hi, k, block)
+// under key (key0, key1).
+struct RngKey {
+  uint32_t idlo, idhi, k, key0, key1;
+};
+
+// Rejection samplers, the alternative to sampling tables (Sec. 3.5): the
+// proposal xi ~ U(0,1] is mapped like the tables' reduced variable (linear
+// for pair, 1/k for brems, 1/eps for Compton) and accepted with the DCS in
+// that variable over its bound (1, 4/3 and 2).  Trial j draws proposal and
+// acceptance from words 2(j%2), 2(j%2)+1 of counter block 3 + j/2; after 64
+// rejections the last proposal stands.  Out of line: inlined into the step
+// kernels it would cost them registers whether or not rejection is chosen.
+constexpr uint32_t kRejBlock0 = 3u;
+constexpr int kRejMaxTrials = 64;
+
+template <typename R>
+__device__ __noinline__ R reject_sample(const View<R> &V, int m, R E, const RngKey &g, R *xi_out, int *trials = nullptr) {
+  const R cut = V.rc.cut[m];
+  const R ME = static_cast<R>(kME);
+  R v = R(0), xi = R(0);
+  uint4 w = make_uint4(0u, 0u, 0u, 0u);
+  int j = 0;
+  for (; j < kRejMaxTrials; ++j) {
+    if ((j & 1) == 0) w = philox4x32_10(make_uint4(g.idlo, g.idhi, g.k, kRejBlock0 + (j >> 1)), g.key0, g.key1);
+    xi = u24<R>((j & 1) ? w.z : w.x);
+    const R ua = u24<R>((j & 1) ? w.w : w.y);
+    v = reduced_to_physical<R>(m, E, xi, cut);
+    R f;
+    if (m == kPair) {
+      f = R(1) - R(4.0 / 3.0) * v * (R(1) - v);
+    } else if (m == kBrem) {
+      const R y = v / (E + ME);
+      f = (R(4.0 / 3.0) - R(4.0 / 3.0) * y + y * y) * R(0.75);
+    } else {  // Compton, 1 - cos theta = (1 - eps)/(kappa eps)
+      const R t = (R(1) - v) / (E / ME * v), s2 = t * (R(2) - t);
+      f = R(0.5) * (R(1) + v * v - v * s2);
+    }
+    if (ua <= f) break;
+  }
+  if (trials) *trials = j < kRejMaxTrials ? j + 1 : kRejMaxTrials;
+  *xi_out = xi;
+  return v;
 }
 
 // u: grid choice, bin + alias, in-bin position
@@ -517,8 +568,8 @@ template <typename R> __device__ __forceinline__ void at_rest(Kids<R> &k, R u6, 
 // without cancellation, written from the sampled xi; they are algebraically
 // the textbook two-body kinematics.
 template <typename R>
-__device__ int interact(const View<R> &V, int type, int p, R &E, R d[3], const R *u, Kids<R> &kids, R &local,
-                        int &npair, int &nann) {
+__device__ int interact(const View<R> &V, int type, int p, R &E, R d[3], const R *u, const RngKey &g, Kids<R> &kids,
+                        R &local, int &npair, int &nann) {
   const R ME = static_cast<R>(kME);
   const R ecut_push = V.rc.ecut_push;
   const R tcut = V.rc.tcut;
@@ -543,7 +594,9 @@ __device__ int interact(const View<R> &V, int type, int p, R &E, R d[3], const R
     model = kAnnih;
   }
   R xi = R(0), v = R(0);
-  if (model >= 0) v = alias_sample<R>(V, model, E, u[2], u[3], u[4], &xi);
+  if (model >= 0)
+    v = (model <= kBrem && E >= V.rc.rej_min[model]) ? reject_sample<R>(V, model, E, g, &xi)
+                                                       : alias_sample<R>(V, model, E, u[2], u[3], u[4], &xi);
   R sp, cp;
   m_sincos(static_cast<R>(2.0 * kPi) * u[5], &sp, &cp);
   if (model == kCompton) {  // eps = eps0^(1-xi)

@@ -300,10 +300,12 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
 template <typename R>
 __device__ __forceinline__ int final_state(const View<R> &V, const DevState<R> *S, BlockCnt *bc, int type, int proc,
                                            R &E, R d[3], const R *u, Kids<R> &kids, unsigned ev, int sub,
-                                           double x, double y, Pending<R> *pd = nullptr) {
+                                           double x, double y, unsigned long long id, uint32_t kk,
+                                           Pending<R> *pd = nullptr) {
   R local;
   int np = 0, na = 0;
-  const int r = interact(V, type, proc, E, d, u, kids, local, np, na);
+  const RngKey g = {static_cast<uint32_t>(id), static_cast<uint32_t>(id >> 32), kk, S->seed_lo ^ ev, S->seed_hi};
+  const int r = interact(V, type, proc, E, d, u, g, kids, local, np, na);
   if (r < 0) return -1;
   if (np) count(S, bc, ev, GV_C_PAIR, np);
   if (na) count(S, bc, ev, GV_C_ANNIH, na);
@@ -735,7 +737,7 @@ __global__ void GV_STEP_BOUNDS
       }
       if (!SORT && alive && proc >= 0) {  // final state in place (warp-divergent across processes)
         R d[3] = {t.u, t.v, t.w};
-        const int r = final_state(V, S, &bc, t.type, proc, t.E, d, u, kids, t.ev, t.sub, t.x, t.y, pd);
+        const int r = final_state(V, S, &bc, t.type, proc, t.E, d, u, kids, t.ev, t.sub, t.x, t.y, t.id, kstep, pd);
         if (r >= 0) {
           t.u = d[0]; t.v = d[1]; t.w = d[2];
           t.flags |= kFlagInteracted;
@@ -826,7 +828,7 @@ __global__ void GV_STEP_BOUNDS
           R d[3] = {q.d0, q.d1, q.d2};
           R e = q.E;
           const int ty = q.tp / 3;
-          const int r = final_state(V, S, &bc, ty, q.tp - 3 * ty, e, d, uu, kb, q.ev, q.sub, q.x, q.y);
+          const int r = final_state(V, S, &bc, ty, q.tp - 3 * ty, e, d, uu, kb, q.ev, q.sub, q.x, q.y, q.id, q.kk);
           par.x = q.x; par.y = q.y; par.z = q.z;
           par.id = q.id;
           par.ev = q.ev;
@@ -1117,7 +1119,7 @@ __global__ void __launch_bounds__(256) interact_kernel(const DevState<R> *__rest
       kk = q.kk;
       t.step = kk + 1;
       t.nlam = R(-1);
-      const int r = final_state(V, S, &bc, ty, proc, e, d, uu, kids, t.ev, t.sub, t.x, t.y);
+      const int r = final_state(V, S, &bc, ty, proc, e, d, uu, kids, t.ev, t.sub, t.x, t.y, q.id, q.kk);
       t.E = e;
       t.u = d[0]; t.v = d[1]; t.w = d[2];
       if (r >= 0) t.flags |= kFlagInteracted;
@@ -1380,6 +1382,10 @@ template <typename R> View<R> make_view(const Ctx *c) {
     v.rc.cut[m] = static_cast<R>(c->meta[m].cut);
   }
   for (int m = 0; m < GV_MAX_MAT; ++m) v.rc.inv_X0[m] = static_cast<R>(c->ht.inv_X0_cm[m]);
+  for (int m = 0; m < kNModel; ++m) {  // a threshold beyond R's range means "never"
+    const double r = c->cuts.reject_min_MeV[m];
+    v.rc.rej_min[m] = r < 1e30 ? static_cast<R>(r) : r_inf_host<R>();
+  }
   v.cut.mask = c->cuts.process_mask;
   return v;
 }

@@ -69,7 +69,9 @@ __global__ void k_interact(View<R> V, int type, int proc, const double *E, const
   kids.n = 0;
   R local = R(0);
   int np = 0, na = 0;
-  const int r = interact(V, type, proc, e, d, uu, kids, local, np, na);
+  // a rejection sampler, where configured, draws from the stream (i, 0, 0) under key (0, 0)
+  const RngKey g = {static_cast<uint32_t>(i), static_cast<uint32_t>(i >> 32), 0u, 0u, 0u};
+  const int r = interact(V, type, proc, e, d, uu, g, kids, local, np, na);
   double *o = out + 24 * i;
   for (int j = 0; j < 24; ++j) o[j] = 0.0;
   o[0] = r == 1 ? static_cast<double>(e) : (r == 0 ? -1.0 : E[i]);
@@ -144,6 +146,26 @@ __global__ void k_field(View<R> V, int type, const double *E, const double *sv, 
     out[7 * i + 3 + j] = nd[j];
   }
   out[7 * i + 6] = field_limit(V, type, e, d[0], d[1], d[2]);
+}
+
+template <typename R>
+__global__ void k_sample(View<R> V, int model, int method, const double *E, long long n, uint32_t k0, uint32_t k1,
+                         double *out) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const RngKey g = {static_cast<uint32_t>(i), static_cast<uint32_t>(i >> 32), 0u, k0, k1};
+  const R e = static_cast<R>(E[i]);
+  R xi, v;
+  int tr = 1;
+  if (method == 1) {
+    v = reject_sample<R>(V, model, e, g, &xi, &tr);
+  } else {
+    const uint4 w = philox4x32_10(make_uint4(g.idlo, g.idhi, 0u, 0u), k0, k1);
+    v = alias_sample<R>(V, model, e, u24<R>(w.x), u24<R>(w.y), u24<R>(w.z), &xi);
+  }
+  out[3 * i] = v;
+  out[3 * i + 1] = xi;
+  out[3 * i + 2] = tr;
 }
 
 int launch_status() { return cudaGetLastError() == cudaSuccess ? GV_OK : GV_ERR_CUDA; }
@@ -232,6 +254,17 @@ int gv_unit_field(void *ctx, int type, const double *E, const double *sv, const 
   if (n == 0) return GV_OK;
   GV_UNIT_DISPATCH((k_field<float><<<blocks_for(n), kThreads, 0, s>>>(vf, type, E, sv, dir, n, out)),
                    (k_field<double><<<blocks_for(n), kThreads, 0, s>>>(vd, type, E, sv, dir, n, out)))
+}
+
+int gv_unit_sample(void *ctx, int model, int method, const double *E, long long n, unsigned long long seed,
+                   double *out, void *stream) {
+  if (!ctx || model < 0 || model >= kNModel || method < 0 || method > 1 || n < 0 || (n > 0 && (!E || !out)))
+    return GV_ERR_BAD_ARG;
+  if (method == 1 && model > kBrem) return GV_ERR_BAD_ARG;  // rejection is built for Compton, pair, brems
+  if (n == 0) return GV_OK;
+  const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+  GV_UNIT_DISPATCH((k_sample<float><<<blocks_for(n), kThreads, 0, s>>>(vf, model, method, E, n, k0, k1, out)),
+                   (k_sample<double><<<blocks_for(n), kThreads, 0, s>>>(vd, model, method, E, n, k0, k1, out)))
 }
 
 }  // extern "C"

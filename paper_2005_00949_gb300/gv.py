@@ -47,7 +47,8 @@ class gv_layers(C.Structure):
 
 class gv_cuts(C.Structure):
     _fields_ = [("gamma_cut_MeV", C.c_double), ("e_cut_MeV", C.c_double),
-                ("track_cut_MeV", C.c_double), ("process_mask", C.c_uint)]
+                ("track_cut_MeV", C.c_double), ("process_mask", C.c_uint),
+                ("reject_min_MeV", C.c_double * 6)]
 
 
 class gv_config(C.Structure):
@@ -99,6 +100,7 @@ def load():
             lib.gv_unit_distance.argtypes = [vp, vp, vp, vp, ll, vp, vp, vp, vp]
             lib.gv_unit_msc.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, ll, vp, vp, vp]
             lib.gv_unit_field.argtypes = [vp, i, vp, vp, vp, ll, vp, vp]
+            lib.gv_unit_sample.argtypes = [vp, i, i, vp, ll, C.c_ulonglong, vp, vp]
             _lib = lib
     return _lib
 
@@ -152,6 +154,8 @@ class Context:
         geo.half_x_cm, geo.half_y_cm, geo.nx_cells, geo.ny_cells = wl.half_x, wl.half_y, wl.nx, wl.ny
         geo.field_T, geo.field_axis = wl.field_T, wl.field_axis
         cuts = gv_cuts(wl.gamma_cut, wl.e_cut, wl.track_cut, wl.process_mask)
+        for m in range(6):
+            cuts.reject_min_MeV[m] = wl.reject_min[m] if wl.reject_min is not None else 1e300
         cfg = config if config is not None else gv_default_config()
         for k, v in overrides.items():
             setattr(cfg, k, v)
@@ -253,6 +257,11 @@ class Context:
     def gv_unit_field(self, ptype, E, s, d, out, stream=None):
         _check(self.lib.gv_unit_field(self.h, ptype, _ptr(E), _ptr(s), _ptr(d), E.numel(), _ptr(out),
                                       _stream_ptr(stream)), "gv_unit_field")
+
+
+    def gv_unit_sample(self, model, method, E, seed, out, stream=None):
+        _check(self.lib.gv_unit_sample(self.h, model, method, _ptr(E), E.numel(), C.c_ulonglong(seed), _ptr(out),
+                                       _stream_ptr(stream)), "gv_unit_sample")
 
 
 def gv_unit_philox(ctr, key, out, stream=None):

@@ -155,3 +155,36 @@ def test_autotuner_keeps_results(gvmod):
     base = _run(gvmod, wl, per_event_counts=1)
     tuned = _run(gvmod, wl, per_event_counts=1, **knobs)
     assert np.array_equal(base["counts"][:, :11], tuned["counts"][:, :11])
+
+
+def test_pair_sampler_timing_rejection_vs_tables(gvmod):
+    """The paper's comparison of rejection and sampling tables for
+    Bethe-Heitler pair production as a function of the photon energy, on
+    the GPU: kernel time of 4M samples each way (CUDA events, best of 5)."""
+    import torch
+    wl = W.pbps_electrons(1)
+    ctx = _ctx(gvmod, wl, stack_capacity=1 << 12)
+    n = 4 << 20
+    out = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+    res = {}
+    for E in (2.0, 5.0, 10.0, 30.0, 100.0, 1e3, 1e4, 1e5):
+        e = torch.full((n,), E, dtype=torch.float64, device="cuda")
+        t = {}
+        for method in (0, 1):
+            best = None
+            for _ in range(5):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                ctx.gv_unit_sample(1, method, e, 99, out)
+                b.record()
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b)
+                best = ms if best is None else min(best, ms)
+            t[method] = best
+            if method == 1:
+                trials = out[:, 2].mean().item()
+        res[str(E)] = {"tables_ms": t[0], "rejection_ms": t[1], "speedup_rejection": t[0] / t[1],
+                       "mean_trials": trials}
+        assert 1.0 <= trials < 1.6
+    ctx.close()
+    _report("pair_sampler_rejection_vs_tables", samples=n, per_energy_MeV=res)

@@ -1,5 +1,5 @@
-"""Showers with multiple scattering (GV_P_MSC) and in a magnetic field
-against the oracle.
+"""Showers with multiple scattering (GV_P_MSC), in a magnetic field and with
+rejection samplers, against the oracle.
 
 The scattering draws its uniforms from counter block 2 of each step on both
 sides, so FP64 histories coincide with the oracle's event by event, and the
@@ -104,4 +104,25 @@ def test_testem3_field_and_msc_paper_conditions(gvmod, oracle_mod):
             edep_Pb_GeV=float(mat[0] / 1e3), edep_LAr_GeV=float(mat[1] / 1e3),
             gammas=float(cnt[4]), electrons=float(cnt[5] - 1), positrons=float(cnt[6]),
             charged_steps=float(cnt[2] + cnt[3]), neutral_steps=float(cnt[1]),
+            layers=_layer_stats(wl, r["edep"], ref["edep"]))
+
+
+# ---------------------------------------------------------------- rejection samplers
+def test_fp64_rejection_showers_follow_oracle_event_by_event(gvmod, oracle_mod):
+    wl = W.with_rejection(W.pbps_electrons(300, 1000.0))
+    r = _run(gvmod, wl, precision=1, per_event_counts=1)
+    ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
+    same = np.all(r["counts"][:, :11] == ref["counts"][:, :11], axis=1)
+    assert same.mean() >= 0.9, same.mean()
+    assert np.abs(r["edep"][same] - ref["edep"][same]).max() < 1e-9 * 1000.0
+
+
+def test_mixed_rejection_showers_and_measured(gvmod, oracle_mod):
+    wl = W.with_rejection(W.config(4))
+    r = _run(gvmod, wl, stack_capacity=1 << 23)
+    ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
+    layer_parity(wl, r["edep"], ref["edep"])
+    c = r["counters"]
+    _report("config4_rejection", events=wl.n_events, kernel_ms=r["kernel_ms"],
+            events_per_s=wl.n_events / (r["kernel_ms"] / 1e3), steps=c["steps"],
             layers=_layer_stats(wl, r["edep"], ref["edep"]))

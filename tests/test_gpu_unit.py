@@ -349,3 +349,29 @@ def test_helix_matches_oracle(torch, fctx, oracle_mod, ptype):
             sa2 = 1.0 - d[i][1] ** 2
             cond = max(1.0, (1e-7 if fctx.prec == 0 else 1e-15) / max(sa2, 1e-300) / tol)
             assert abs(g[i, 6] - sl) <= tol * sl * cond, (i, g[i, 6], sl, sa2)
+
+
+# ---------------------------------------------------------------- rejection samplers
+@pytest.mark.parametrize("model", [0, 1, 2], ids=["compton", "pair", "brems"])
+def test_rejection_sampler_matches_oracle(torch, ctx, oracle_pbps, model):
+    """Same counter-based trials on both sides: the same proposal is accepted
+    unless FP32 rounding flips an acceptance test at its knife edge."""
+    rng = np.random.default_rng(90 + model)
+    lo = {0: 1e-3, 1: 1.1, 2: 1.05}[model]
+    E = 10.0 ** rng.uniform(math.log10(lo), 6, N)
+    seed = 0x0123456789
+    out = torch.zeros((N, 3), dtype=torch.float64, device="cuda")
+    ctx.gv_unit_sample(model, 1, _dev(torch, E), seed, out)
+    g = out.cpu().numpy()
+    tol = TOL[ctx.prec]
+    sel = np.random.default_rng(3).choice(N, 20000, False)
+    mism = 0
+    for i in sel:
+        v, xi, tr = oracle_pbps.reject_sample(model, E[i], (i, 0, 0, seed & 0xffffffff, seed >> 32))
+        if int(g[i, 2]) != tr:
+            mism += 1
+            continue
+        assert abs(g[i, 1] - xi) <= tol, (i, g[i], xi)
+        assert abs(g[i, 0] - v) <= tol * max(abs(v), 1e-3 if model == 0 else abs(v)), (i, g[i], v)
+    assert mism <= (20 if ctx.prec == 0 else 0), mism
+    assert g[:, 2].min() >= 1 and g[:, 2].max() < 64

@@ -101,6 +101,8 @@ def _load():
             lib.or_distance.argtypes = [p, p, p, i, C.POINTER(i), C.POINTER(i)]
             lib.or_interact.argtypes = [p, i, i, d, p, p, p, p]
             lib.or_has_rejection.argtypes = [i]
+            lib.or_sigma_max.restype = d
+            lib.or_sigma_max.argtypes = [p, i, i, d]
             lib.or_reject_sample.restype = d
             lib.or_reject_sample.argtypes = [p, i, d, p, C.POINTER(d), C.POINTER(i)]
             lib.or_safety.restype = d
@@ -254,6 +256,10 @@ class Oracle:
         out = np.zeros(24)
         r = self.lib.or_interact(self.h, ptype, proc, E, _ptr(dd), _ptr(uu), _ptr(rr), _ptr(out))
         return r, out
+
+    def sigma_max(self, ptype: int, mat: int, E) -> np.ndarray:
+        E = np.atleast_1d(np.asarray(E, dtype=np.float64))
+        return np.array([self.lib.or_sigma_max(self.h, ptype, mat, float(e)) for e in E])
 
     @staticmethod
     def has_rejection(model: int) -> bool:

@@ -74,6 +74,9 @@ struct or_ctx {
   int *smat;            /* material of each sub-slab */
   /* tables[type][q][mat][node] */
   double tab[3][4][OR_MAX_MAT][GRID_N];
+  /* integral approach: running maximum over the nodes below of the total
+   * cross section of e- (0) and e+ (1) */
+  double smax[2][OR_MAX_MAT][GRID_N];
   oalias alias[OR_NMODEL];
   double gl_x[16], gl_w[16];
 };
@@ -647,9 +650,18 @@ static void build_tables(or_ctx *c) {
         R += inv_dedx_integral(c, t, m, or_grid_energy(i), or_grid_energy(i + 1));
         c->tab[t][qR][m][i + 1] = R;
       }
+      /* the running maximum of the node values of Sigma(E) */
+      double run = 0.0;
+      for (int i = 0; i < GRID_N; ++i) {
+        double sig = 0.0;
+        for (int p = 0; p < n_proc(t); ++p) sig += c->tab[t][p][m][i];
+        run = fmax(run, sig);
+        c->smax[t - 1][m][i] = run;
+      }
     }
   }
 }
+
 
 double or_table_node(const or_ctx *c, int type, int q, int mat, int i) { return c->tab[type][q][mat][i]; }
 
@@ -670,6 +682,18 @@ double or_table_lookup(const or_ctx *c, int type, int q, int mat, double E) {
   double f;
   grid_pos(E, &i, &f);
   const double *v = c->tab[type][q][mat];
+  return v[i] + f * (v[i + 1] - v[i]);
+}
+
+/* Integral approach (charged tracks lose energy along a step, so their
+ * cross section changes): Sigma_max(E), the linear interpolation of the
+ * running maximum of the node values, bounds the interpolated Sigma at every
+ * energy up to E (node-wise >= with the same weights, and non-decreasing). */
+double or_sigma_max(const or_ctx *c, int type, int mat, double E) {
+  int i;
+  double f;
+  grid_pos(E, &i, &f);
+  const double *v = c->smax[type - 1][mat];
   return v[i] + f * (v[i + 1] - v[i]);
 }
 
@@ -1225,9 +1249,13 @@ static void run_event(const job_t *J, long ev, ostack *st) {
       if (t.nlam <= 0.0) t.nlam = -log(u[0]);
       double sig[3] = {0, 0, 0}, Sig = 0.0;
       for (int p = 0; p < np; ++p) { sig[p] = or_table_lookup(c, t.type, p, mat, t.E); Sig += sig[p]; }
-      double s_phys = Sig > 0.0 ? t.nlam / Sig : INFINITY;
-      double s_cont = INFINITY;
       int charged = t.type != OR_GAMMA;
+      /* integral approach: the step is drawn with Sigma_max over the energies
+       * the track can reach, the interaction accepted at the post-step point */
+      const int integral = charged && (s->process_mask & OR_P_INTEGRAL);
+      const double Smax = integral ? or_sigma_max(c, t.type, mat, t.E) : Sig;
+      double s_phys = Smax > 0.0 ? t.nlam / Smax : INFINITY;
+      double s_cont = INFINITY;
       if (charged) {
         double R = or_table_lookup(c, t.type, t.type == OR_ELECTRON ? 2 : 3, mat, t.E);
         s_cont = fmax(STEP_ALPHA_R * R, fmin(STEP_RHO_F, R));
@@ -1267,7 +1295,7 @@ static void run_event(const job_t *J, long ev, ostack *st) {
         else if (plane == -2) t.pos[0] = pre_dir[0] > 0.0 ? s->half_x : -s->half_x;
         else if (plane == -3) t.pos[1] = pre_dir[1] > 0.0 ? s->half_y : -s->half_y;
       }
-      if (Sig > 0.0) t.nlam = (lim == 1) ? 0.0 : t.nlam - sstep * Sig;
+      if (Smax > 0.0) t.nlam = (lim == 1) ? 0.0 : t.nlam - sstep * Smax;
       t.step = k + 1;
       cnt[OR_C_STEPS] += 1;
       cnt[OR_C_STEPS_G + t.type] += 1;
@@ -1330,13 +1358,21 @@ static void run_event(const job_t *J, long ev, ostack *st) {
       /* PostStepActions: discrete interaction */
       double target = u[1] * Sig, cum = 0.0;
       int proc = -1;
-      for (int p = 0; p < np; ++p) {
-        cum += sig[p];
-        if (target < cum) { proc = p; break; }
+      if (integral) { /* post-step cross sections; above their sum: no interaction */
+        target = u[1] * Smax;
+        for (int p = 0; p < np; ++p) {
+          cum += or_table_lookup(c, t.type, p, mat, t.E);
+          if (target < cum) { proc = p; break; }
+        }
+      } else {
+        for (int p = 0; p < np; ++p) {
+          cum += sig[p];
+          if (target < cum) { proc = p; break; }
+        }
+        if (proc < 0)
+          for (int p = np - 1; p >= 0; --p)
+            if (sig[p] > 0.0) { proc = p; break; }
       }
-      if (proc < 0)
-        for (int p = np - 1; p >= 0; --p)
-          if (sig[p] > 0.0) { proc = p; break; }
       t.nlam = -1.0;
       if (proc < 0) continue;
       ctr[3] = 1u;

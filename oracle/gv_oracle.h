@@ -51,7 +51,8 @@ enum { OR_GAMMA = 0, OR_ELECTRON = 1, OR_POSITRON = 2 };
 enum {
   OR_P_COMPTON = 1u << 0, OR_P_PHOTO = 1u << 1, OR_P_PAIR = 1u << 2,
   OR_P_BREM = 1u << 3, OR_P_IONI = 1u << 4, OR_P_ANNIH = 1u << 5,
-  OR_P_MSC = 1u << 6  /* Gaussian multiple scattering of e+- (along the step) */
+  OR_P_MSC = 1u << 6,  /* Gaussian multiple scattering of e+- (along the step) */
+  OR_P_INTEGRAL = 1u << 7  /* integral approach for the e+- cross sections along a step */
 };
 
 /* alias-sampled final-state models */
@@ -118,6 +119,7 @@ double or_grid_energy(int i);
 double or_table_node(const or_ctx *c, int type, int q, int mat, int i);
 double or_table_lookup(const or_ctx *c, int type, int q, int mat, double E);
 double or_eloss(const or_ctx *c, int type, int mat, double E, double s); /* post-step energy */
+double or_sigma_max(const or_ctx *c, int type, int mat, double E); /* integral approach bound */
 
 /* --- alias sampling tables ------------------------------------------- */
 int or_alias_info(const or_ctx *c, int model, double *E_lo, int *n_E);

@@ -23,6 +23,7 @@ GAMMA, ELECTRON, POSITRON = 0, 1, 2
 P_COMPTON, P_PHOTO, P_PAIR, P_BREM, P_IONI, P_ANNIH = (1 << i for i in range(6))
 P_ALL = P_COMPTON | P_PHOTO | P_PAIR | P_BREM | P_IONI | P_ANNIH
 P_MSC = 1 << 6  # multiple scattering along charged steps (not part of P_ALL)
+P_INTEGRAL = 1 << 7  # integral approach for e+- cross sections along a step (not part of P_ALL)
 
 DEFAULT_SEED = 0x6765616E7456  # "geantV"
 
@@ -183,6 +184,11 @@ def with_rejection(wl: Workload, reject_min=(0.0, 0.0, 0.0, math.inf, math.inf, 
     """The same workload sampling Compton, pair and bremsstrahlung final states
     by rejection above the given energies (MeV), instead of sampling tables."""
     return dataclasses.replace(wl, reject_min=tuple(reject_min), name=wl.name + "_rej")
+
+
+def with_integral(wl: Workload) -> Workload:
+    """The same workload with the integral approach for charged tracks."""
+    return dataclasses.replace(wl, process_mask=wl.process_mask | P_INTEGRAL, name=wl.name + "_int")
 
 
 def with_msc(wl: Workload) -> Workload:

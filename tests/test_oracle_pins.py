@@ -738,3 +738,41 @@ def test_showers_agree_between_samplers(oracle_mod):
     res = (b["edep"].sum(1) + b["escape"] - (2000.0 + 2 * ME * (c[:, 8] - c[:, 7]))) / 2000.0
     assert np.abs(res).max() < 1e-9
     assert not np.array_equal(a["counts"], c)  # the samplers did differ
+
+
+# ---------------------------------------------------------------- integral approach
+def test_sigma_max_bounds_the_cross_section_below(oracle_mod):
+    """Sigma_max(E) >= Sigma(E') for every E' <= E (interpolated tables), so
+    thinning with it samples the interaction points of the changing Sigma."""
+    for wl in (W.pbps_electrons(1), W.wsi_cells(1)):
+        o = oracle_mod.Oracle(wl)
+        rng = np.random.default_rng(12)
+        for ptype, nproc in ((W.ELECTRON, 2), (W.POSITRON, 3)):
+            for mat in range(len(wl.materials)):
+                E = 10.0 ** rng.uniform(-3, 6, 400)
+                Ep = E * rng.uniform(0, 1, 400)
+                smax = o.sigma_max(ptype, mat, E)
+                sig_p = sum(o.lookup(ptype, p, mat, Ep) for p in range(nproc))
+                sig = sum(o.lookup(ptype, p, mat, E) for p in range(nproc))
+                assert np.all(smax >= sig_p * (1 - 1e-12)) and np.all(smax >= sig * (1 - 1e-12))
+                grid = oracle_mod.Oracle.grid()
+                sm = o.sigma_max(ptype, mat, grid)
+                assert np.all(np.diff(sm) >= 0)
+
+
+def test_integral_approach_showers_agree(oracle_mod):
+    wl = W.pbps_mixed(2000).subset(2000)
+    wl.primaries["E"] = np.minimum(wl.primaries["E"], 3000.0)
+    a = oracle_mod.Oracle(wl).transport(n_threads=4)
+    b = oracle_mod.Oracle(W.with_integral(wl)).transport(n_threads=4)
+    ga = a["edep"].reshape(2000, 50, 2).sum(2)
+    gb = b["edep"].reshape(2000, 50, 2).sum(2)
+    comb = np.sqrt(ga.var(0, ddof=1) / 2000 + gb.var(0, ddof=1) / 2000)
+    pull = np.abs(ga.mean(0) - gb.mean(0))[comb > 0] / comb[comb > 0]
+    assert pull.max() < 4.0, pull.max()
+    c = b["counts"]
+    T0 = np.zeros(2000)
+    np.add.at(T0, wl.primaries["event"], wl.primaries["E"])
+    res = (b["edep"].sum(1) + b["escape"] - (T0 + 2 * ME * (c[:, 8] - c[:, 7]))) / T0
+    assert np.abs(res).max() < 1e-9
+    assert not np.array_equal(a["counts"], c)

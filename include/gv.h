@@ -47,6 +47,9 @@ extern "C" {
 #define GV_P_IONI (1u << 4)
 #define GV_P_ANNIH (1u << 5)
 #define GV_P_MSC (1u << 6)   /* Gaussian multiple scattering of e+- along the step (off by default) */
+#define GV_P_INTEGRAL (1u << 7) /* integral approach for e+- cross sections along a step (off by default):
+                                   steps drawn with the running maximum of Sigma below E, interactions
+                                   accepted with the post-step cross sections */
 
 /* arithmetic of the stepping loop */
 #define GV_MIXED 0 /* FP32 physics, tables and energies; FP64 positions and boundaries */

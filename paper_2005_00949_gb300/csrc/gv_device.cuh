@@ -99,6 +99,7 @@ template <typename R> struct View {
   const double *zb;          // nsub+1 planes
   const unsigned char *smat; // material of each sub-slab
   const AliasBin<R> *bins;   // all models, [off + ie*kNB + j]
+  const R *smax;             // integral approach bound [(mat*2 + type-1)*kGridN + node], smem or global
   ModelMeta meta[kNModel];
   GeoConst geo;
   CutConst cut;

@@ -44,6 +44,9 @@ struct HostTables {
   std::vector<float> a_q[kNModel];     // [nE][kNB]
   std::vector<int> a_alias[kNModel];   // [nE][kNB]
   double inv_X0_cm[GV_MAX_MAT] = {0, 0, 0, 0};  // 1 / radiation length per material, 1/cm
+  // integral approach: running maximum over the nodes below of the total
+  // e- (0) and e+ (1) cross section, smax[(m*2 + pos)*kGridN + i]
+  std::vector<double> smax;
 };
 
 int build_host_tables(const gv_material *mats, int n_mats, const gv_cuts &cuts, HostTables *out,

@@ -99,6 +99,7 @@ template <typename R> struct DevState {
   int n_mat;
   unsigned xs_bytes, zb_bytes;  // staged into shared memory
   unsigned smem_req_off;        // start of the basketizer's request records
+  unsigned smax_off, smax_bytes; // the integral approach's bound, staged into shared memory
 };
 
 }  // namespace gv

@@ -321,6 +321,7 @@ int build_host_tables(const gv_material *mats, int n_mats, const gv_cuts &cuts, 
   GL20 gl;
   out->n_mat = n_mats;
   out->xs.assign(static_cast<size_t>(n_mats) * 3 * kGridN * 4, 0.0);
+  out->smax.assign(static_cast<size_t>(n_mats) * 2 * kGridN, 0.0);
   const unsigned pm = cuts.process_mask;
   for (int m = 0; m < n_mats; ++m) {
     const Medium md = make_medium(mats[m]);
@@ -364,6 +365,12 @@ int build_host_tables(const gv_material *mats, int n_mats, const gv_cuts &cuts, 
         }
         R += path_length(md, pos, grid_energy(i - 1), grid_energy(i), cuts, gl);
         at(type, i, q) = R;
+      }
+      double run = 0.0;  // the bound of the integral approach
+      for (int i = 0; i < kGridN; ++i) {
+        const double sig = at(type, i, 0) + at(type, i, 1) + (pos ? at(type, i, 2) : 0.0);
+        run = std::max(run, sig);
+        out->smax[(static_cast<size_t>(m) * 2 + pos) * kGridN + i] = run;
       }
     }
   }

@@ -115,6 +115,26 @@ template <typename R> struct Trk {
 
 __device__ __forceinline__ void set_status(Ctl *ctl, int code) { atomicCAS(&ctl->status, 0, code); }
 
+// Integral approach at the post-step point: the process whose cumulative
+// post-step cross section first exceeds `target` (u Sigma_max), or -1 (no
+// interaction) above their sum.  Out of line: the option would otherwise
+// cost every step kernel registers.
+template <typename R> __device__ __noinline__ int integral_choice(const View<R> &V, int mat, int type, R E, R target) {
+  int i;
+  R f;
+  grid_pos(V, E, i, f);
+  const V4<R> p4 = lookup_at(V, mat, type, i, f);
+  R cum = p4.x;
+  if (target < cum) return 0;
+  cum += p4.y;
+  if (target < cum) return 1;
+  if (type == 2) {
+    cum += p4.z;
+    if (target < cum) return 2;
+  }
+  return -1;
+}
+
 // ------------------------------------------------------------------ one step
 // PreStep .. process choice of one step.  Returns 1 if the track is still
 // alive; then proc >= 0 names the discrete process due at the post-step
@@ -161,9 +181,18 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   const R sig0 = s4.x, sig1 = s4.y, sig2 = (t.type == 1) ? R(0) : s4.z;
   const R Sig = sig0 + sig1 + sig2;
   const R INF = r_inf<R>();
-  const R s_phys = Sig > R(0) ? q_div(t.nlam, Sig) : INF;
-  R s_cont = INF;
   const bool charged = t.type != 0;
+  // integral approach: the step is drawn with the bound Sigma_max(E) of the
+  // cross sections the track can reach; the interaction is accepted at the
+  // post-step point
+  const bool integral = charged && (V.cut.mask & GV_P_INTEGRAL);
+  R Smax = Sig;
+  if (integral) {
+    const R *m = V.smax + (mat * 2 + t.type - 1) * kGridN;
+    Smax = m[gi] + gf * (m[gi + 1] - m[gi]);
+  }
+  const R s_phys = Smax > R(0) ? q_div(t.nlam, Smax) : INF;
+  R s_cont = INF;
   if (charged) {
     const R Rr = t.type == 1 ? s4.z : s4.w;
     const R a = static_cast<R>(kAlphaR) * Rr, b = Rr < static_cast<R>(kRhoF) ? Rr : static_cast<R>(kRhoF);
@@ -222,7 +251,7 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
       else if (plane == -3) t.y = V.geo.wy[t.v > R(0) ? 1 : 0];
     }
   }
-  if (Sig > R(0)) t.nlam = (lim == 1) ? R(0) : t.nlam - s * Sig;
+  if (Smax > R(0)) t.nlam = (lim == 1) ? R(0) : t.nlam - s * Smax;
   t.step = k + 1;
   // the block's step counters are summed per warp by the caller; only the
   // optional per-event rows are booked here
@@ -271,19 +300,23 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   if (lim != 1) return 1;
   // PostStepActions: process choice, then the final state
   if (!have_r0) r0 = philox4x32_10(make_uint4(idlo, idhi, k, 0u), key0, key1);
-  const R target = u24<R>(r0.y) * Sig;
   int proc = -1;
-  R cum = sig0;
-  if (target < cum) proc = 0;
-  else {
-    cum += sig1;
-    if (target < cum) proc = 1;
+  if (integral) {  // post-step cross sections; above their sum: no interaction
+    proc = integral_choice(V, mat, t.type, t.E, u24<R>(r0.y) * Smax);
+  } else {
+    const R target = u24<R>(r0.y) * Sig;
+    R cum = sig0;
+    if (target < cum) proc = 0;
     else {
-      cum += sig2;
-      if (target < cum) proc = 2;
+      cum += sig1;
+      if (target < cum) proc = 1;
+      else {
+        cum += sig2;
+        if (target < cum) proc = 2;
+      }
     }
+    if (proc < 0) proc = sig2 > R(0) ? 2 : (sig1 > R(0) ? 1 : (sig0 > R(0) ? 0 : -1));
   }
-  if (proc < 0) proc = sig2 > R(0) ? 2 : (sig1 > R(0) ? 1 : (sig0 > R(0) ? 0 : -1));
   t.nlam = R(-1);
   if (proc < 0) return 1;
   const uint4 r1 = philox4x32_10(make_uint4(idlo, idhi, k, 1u), key0, key1);
@@ -584,12 +617,18 @@ __global__ void GV_STEP_BOUNDS
     for (int i = tid; i < kGridN; i += blockDim.x) idst[i] = S->view.inv_node[i];
     unsigned char *mdst = smem + S->xs_bytes + S->zb_bytes + kInvNodeBytes;
     for (int i = tid; i < S->view.geo.nsub; i += blockDim.x) mdst[i] = S->view.smat[i];
+    {
+      const uint4 *ssrc = reinterpret_cast<const uint4 *>(S->view.smax);
+      uint4 *sdst = reinterpret_cast<uint4 *>(smem + S->smax_off);
+      for (unsigned i = tid; i < S->smax_bytes / 16; i += blockDim.x) sdst[i] = ssrc[i];
+    }
     if (tid == 0) {
       sV = S->view;
       sV.xs = reinterpret_cast<const V4<R> *>(smem);
       sV.zb = zdst;
       sV.inv_node = idst;
       sV.smat = mdst;
+      sV.smax = reinterpret_cast<const R *>(smem + S->smax_off);
       for (int i = 0; i < 4; ++i) s_end[i] = ctl->chunk_end[i];
       for (int r = 0; r <= kNClaim; ++r)
         s_slice[r] = static_cast<unsigned>((static_cast<unsigned long long>(s_end[3]) * r) / kNClaim);
@@ -939,12 +978,18 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_ALONG_MIN_BLOCKS : 2)
     for (int i = tid; i < kGridN; i += blockDim.x) idst[i] = S->view.inv_node[i];
     unsigned char *mdst = smem + S->xs_bytes + S->zb_bytes + kInvNodeBytes;
     for (int i = tid; i < S->view.geo.nsub; i += blockDim.x) mdst[i] = S->view.smat[i];
+    {
+      const uint4 *ssrc = reinterpret_cast<const uint4 *>(S->view.smax);
+      uint4 *sdst = reinterpret_cast<uint4 *>(smem + S->smax_off);
+      for (unsigned i = tid; i < S->smax_bytes / 16; i += blockDim.x) sdst[i] = ssrc[i];
+    }
     if (tid == 0) {
       sV = S->view;
       sV.xs = reinterpret_cast<const V4<R> *>(smem);
       sV.zb = zdst;
       sV.inv_node = idst;
       sV.smat = mdst;
+      sV.smax = reinterpret_cast<const R *>(smem + S->smax_off);
       for (int i = 0; i < 4; ++i) s_end[i] = ctl->chunk_end[i];
       s_pb = ctl->prim_begin;
       s_K = ctl->K;
@@ -1169,7 +1214,7 @@ struct Ctx {
   bool tables = false;
   HostTables ht;
   // device allocations
-  void *d_xs = nullptr, *d_bins = nullptr;
+  void *d_xs = nullptr, *d_bins = nullptr, *d_smax = nullptr;
   float *d_inv_node = nullptr;
   double *d_zb = nullptr;
   unsigned char *d_smat = nullptr;
@@ -1190,7 +1235,7 @@ struct Ctx {
   long long launches = 0;
   int last_status = 0;
   ModelMeta meta[kNModel];
-  size_t xs_bytes = 0, zb_bytes = 0, smem_bytes = 0, req_off = 0, bins_bytes = 0;
+  size_t xs_bytes = 0, zb_bytes = 0, smem_bytes = 0, req_off = 0, bins_bytes = 0, smax_bytes = 0, smax_off = 0;
   int grid = 0, grid_b = 0;
   // split pipeline: interaction requests and their per-key index lists
   void *d_req = nullptr;
@@ -1319,6 +1364,13 @@ template <typename R> int upload_tables(Ctx *c) {
         bins.push_back(b);
       }
   }
+  {  // the integral approach's bound
+    std::vector<R> sm(h.smax.size());
+    for (size_t i = 0; i < sm.size(); ++i) sm[i] = static_cast<R>(h.smax[i]);
+    c->smax_bytes = (sm.size() * sizeof(R) + 15) / 16 * 16;
+    CK(cudaMalloc(&c->d_smax, c->smax_bytes));
+    CK(cudaMemcpy(c->d_smax, sm.data(), sm.size() * sizeof(R), cudaMemcpyHostToDevice));
+  }
   c->bins_bytes = bins.size() * sizeof(AliasBin<R>);
   CK(cudaMalloc(&c->d_bins, c->bins_bytes));
   CK(cudaMemcpy(c->d_bins, bins.data(), c->bins_bytes, cudaMemcpyHostToDevice));
@@ -1349,6 +1401,7 @@ template <typename R> View<R> make_view(const Ctx *c) {
   v.zb = c->d_zb;
   v.smat = c->d_smat;
   v.bins = reinterpret_cast<const AliasBin<R> *>(c->d_bins);
+  v.smax = reinterpret_cast<const R *>(c->d_smax);
   for (int m = 0; m < kNModel; ++m) v.meta[m] = c->meta[m];
   v.geo.nsub = c->nsub;
   v.geo.nsub_layer = c->geo.n_sub;
@@ -1414,7 +1467,8 @@ template <typename R> int prepare_device(Ctx *c) {
   CK(cudaMalloc(&c->d_state, sizeof(DevState<R>)));
   CK(cudaMallocHost(&c->h_ctl, sizeof(Ctl)));
   c->zb_bytes = ((c->nsub + 1) * sizeof(double) + 15) / 16 * 16;
-  c->req_off = c->xs_bytes + c->zb_bytes + kInvNodeBytes + (c->nsub + 15) / 16 * 16;
+  c->smax_off = c->xs_bytes + c->zb_bytes + kInvNodeBytes + (c->nsub + 15) / 16 * 16;
+  c->req_off = c->smax_off + c->smax_bytes;
   if (c->cfg.pipeline) {
     const size_t rc_ = static_cast<size_t>(cap);
     if (cudaMalloc(&c->d_req, rc_ * sizeof(GReq<R>)) != cudaSuccess ||
@@ -1471,6 +1525,8 @@ template <typename R> DevState<R> make_state(Ctx *c) {
   s.xs_bytes = static_cast<unsigned>(c->xs_bytes);
   s.zb_bytes = static_cast<unsigned>(c->zb_bytes);
   s.smem_req_off = static_cast<unsigned>(c->req_off);
+  s.smax_off = static_cast<unsigned>(c->smax_off);
+  s.smax_bytes = static_cast<unsigned>(c->smax_bytes);
   return s;
 }
 
@@ -1800,6 +1856,7 @@ void gv_destroy(void *ctx) {
   cudaFree(c->d_xs);
   cudaFree(c->d_inv_node);
   cudaFree(c->d_bins);
+  cudaFree(c->d_smax);
   cudaFree(c->d_zb);
   cudaFree(c->d_smat);
   cudaFree(c->d_queues);

@@ -1,5 +1,6 @@
-"""Showers with multiple scattering (GV_P_MSC), in a magnetic field and with
-rejection samplers, against the oracle.
+"""Showers with multiple scattering (GV_P_MSC), in a magnetic field, with
+rejection samplers and with the integral approach (GV_P_INTEGRAL), against
+the oracle.
 
 The scattering draws its uniforms from counter block 2 of each step on both
 sides, so FP64 histories coincide with the oracle's event by event, and the
@@ -125,4 +126,27 @@ def test_mixed_rejection_showers_and_measured(gvmod, oracle_mod):
     c = r["counters"]
     _report("config4_rejection", events=wl.n_events, kernel_ms=r["kernel_ms"],
             events_per_s=wl.n_events / (r["kernel_ms"] / 1e3), steps=c["steps"],
+            layers=_layer_stats(wl, r["edep"], ref["edep"]))
+
+
+# ---------------------------------------------------------------- integral approach
+def test_fp64_integral_showers_follow_oracle_event_by_event(gvmod, oracle_mod):
+    wl = W.with_integral(W.pbps_mixed(300).subset(300))
+    wl.primaries["E"] = np.minimum(wl.primaries["E"], 3000.0)
+    r = _run(gvmod, wl, precision=1, per_event_counts=1)
+    ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
+    same = np.all(r["counts"][:, :11] == ref["counts"][:, :11], axis=1)
+    assert same.mean() >= 0.9, same.mean()
+    assert np.abs(r["edep"][same] - ref["edep"][same]).max() < 1e-9 * 3000.0
+
+
+def test_mixed_integral_showers_and_measured(gvmod, oracle_mod):
+    wl = W.with_integral(W.config(4))
+    r = _run(gvmod, wl, stack_capacity=1 << 23, per_event_counts=1)
+    ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
+    layer_parity(wl, r["edep"], ref["edep"])
+    assert np.abs(_conservation(wl, r)).max() < 1e-5
+    c = r["counters"]
+    _report("config4_integral", events=wl.n_events, kernel_ms=r["kernel_ms"],
+            events_per_s=wl.n_events / (r["kernel_ms"] / 1e3), steps=c["steps"], discrete=c["discrete"],
             layers=_layer_stats(wl, r["edep"], ref["edep"]))

@@ -11,7 +11,7 @@ Between timed steps L2 is flushed by writing a 512 MiB buffer.  Under torchrun
 each rank transports its own 2000-event shard (weak scaling, no collective on
 the data path); rank 0 prints one JSON line.
 
---impl reference times the FP64 CPU oracle (the reference arm of this build)
+--impl reference times the FP64 CPU oracle (the reference arm of this benchmark)
 on a bounded sample of the same workload on the host cores.
 """
 from __future__ import annotations
@@ -208,7 +208,7 @@ def run_reference(args):
             "ms_per_step": 1000.0 * sum(times) / len(times) * (N_EVENTS / n_ev),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "pbps50_e-10GeV_2000ev (config 4)", "events_per_step": N_EVENTS,
+            "config": {"workload": "e-10GeV_PbPS50_2000: 2000 x 10 GeV e- on 50 x (2 mm Pb + 5 mm polystyrene)", "events_per_step": N_EVENTS,
                        "sample_events_per_step": n_ev, "parallelism": "host threads"},
             "cpu_baseline": {"value": v, "unit": "showers/s", "cores": nthr, "kind": "oracle",
                              "sample": f"{n_ev} events per step of the 2000-event workload"},
@@ -336,7 +336,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": "pbps50_e-10GeV_2000ev (config 4): 2000 x 10 GeV e- on "
+        "config": {"workload": "e-10GeV_PbPS50_2000: 2000 x 10 GeV e- on "
                                "50 x (2 mm Pb + 5 mm polystyrene), 40x40 cm, cuts 1 MeV",
                    "events_per_gpu": wl.n_events, "precision": "mixed FP32 physics / FP64 positions",
                    "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"events x{world}"},

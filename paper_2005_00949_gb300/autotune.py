@@ -119,13 +119,14 @@ def load_or_tune(wl: W.Workload, path: str = TUNED_PATH, sample_events: int = 40
 def main(argv=None):
     import argparse
     ap = argparse.ArgumentParser(description="tune the transport launch shape for a workload")
-    ap.add_argument("--config", type=int, default=4, help="workload number (workloads.CONFIGS)")
+    ap.add_argument("--workload", default=W.PBPS_10GEV, choices=sorted(W.STANDARD),
+                    help="standard workload (workloads.STANDARD)")
     ap.add_argument("--sample-events", type=int, default=400)
     ap.add_argument("--budget-s", type=float, default=120.0)
     ap.add_argument("--path", default=TUNED_PATH)
     ap.add_argument("--force", action="store_true")
     a = ap.parse_args(argv)
-    wl = W.config(a.config)
+    wl = W.standard(a.workload)
     if a.force and os.path.exists(a.path):
         with open(a.path) as f:
             db = json.load(f)

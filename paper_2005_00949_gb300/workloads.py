@@ -196,14 +196,16 @@ def with_msc(wl: Workload) -> Workload:
     return dataclasses.replace(wl, process_mask=wl.process_mask | P_MSC, name=wl.name + "_msc")
 
 
-CONFIGS = {
-    1: lambda: photon_slab(100_000, 1.0),
-    2: lambda: pbps_electrons(1000, 1000.0),
-    3: lambda: pbps_mixed(4096),
-    4: lambda: pbps_electrons(2000, 10_000.0),
-    5: lambda: wsi_cells(10_000, 100_000.0),
+# The standard workloads, by name.
+STANDARD = {
+    "gamma1MeV_water10cm_1e5": lambda: photon_slab(100_000, 1.0),
+    "e-1GeV_PbPS50_1000": lambda: pbps_electrons(1000, 1000.0),
+    "mixed0.1-100GeV_PbPS50_4096": lambda: pbps_mixed(4096),
+    "e-10GeV_PbPS50_2000": lambda: pbps_electrons(2000, 10_000.0),
+    "e-100GeV_WSi50_cells_1e4": lambda: wsi_cells(10_000, 100_000.0),
 }
+PHOTON_SLAB, PBPS_1GEV, PBPS_MIXED, PBPS_10GEV, WSI_100GEV = STANDARD
 
 
-def config(k: int) -> Workload:
-    return CONFIGS[k]()
+def standard(name: str) -> Workload:
+    return STANDARD[name]()

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from paper_2005_00949_gb300 import workloads as W
-from test_gpu_configs import _conservation, _layer_stats, _report, _run
+from test_gpu_workloads import _conservation, _layer_stats, _report, _run
 from test_gpu_transport import NTHR, _ctx, gvmod, layer_parity  # noqa: F401
 
 pytestmark = pytest.mark.gpu
@@ -69,12 +69,12 @@ def test_msc_testem3_and_bench_workload_measured(gvmod, oracle_mod):
             gammas=float(cnt[4]), electrons=float(cnt[5] - 1), positrons=float(cnt[6]),
             charged_steps=float(cnt[2] + cnt[3]), neutral_steps=float(cnt[1]),
             layers=_layer_stats(wl, r["edep"], ref["edep"]))
-    wl4 = W.with_msc(W.config(4))
+    wl4 = W.with_msc(W.standard(W.PBPS_10GEV))
     r4 = _run(gvmod, wl4, stack_capacity=1 << 23)
     ref4 = oracle_mod.Oracle(wl4).transport(n_threads=NTHR)
     layer_parity(wl4, r4["edep"], ref4["edep"])
     c = r4["counters"]
-    _report("config4_msc", events=wl4.n_events, kernel_ms=r4["kernel_ms"],
+    _report("e-10GeV_PbPS50_msc", events=wl4.n_events, kernel_ms=r4["kernel_ms"],
             events_per_s=wl4.n_events / (r4["kernel_ms"] / 1e3), steps_per_s=c["steps"] / (r4["kernel_ms"] / 1e3),
             steps=c["steps"], layers=_layer_stats(wl4, r4["edep"], ref4["edep"]))
 
@@ -119,12 +119,12 @@ def test_fp64_rejection_showers_follow_oracle_event_by_event(gvmod, oracle_mod):
 
 
 def test_mixed_rejection_showers_and_measured(gvmod, oracle_mod):
-    wl = W.with_rejection(W.config(4))
+    wl = W.with_rejection(W.standard(W.PBPS_10GEV))
     r = _run(gvmod, wl, stack_capacity=1 << 23)
     ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
     layer_parity(wl, r["edep"], ref["edep"])
     c = r["counters"]
-    _report("config4_rejection", events=wl.n_events, kernel_ms=r["kernel_ms"],
+    _report("e-10GeV_PbPS50_rejection", events=wl.n_events, kernel_ms=r["kernel_ms"],
             events_per_s=wl.n_events / (r["kernel_ms"] / 1e3), steps=c["steps"],
             layers=_layer_stats(wl, r["edep"], ref["edep"]))
 
@@ -141,12 +141,12 @@ def test_fp64_integral_showers_follow_oracle_event_by_event(gvmod, oracle_mod):
 
 
 def test_mixed_integral_showers_and_measured(gvmod, oracle_mod):
-    wl = W.with_integral(W.config(4))
+    wl = W.with_integral(W.standard(W.PBPS_10GEV))
     r = _run(gvmod, wl, stack_capacity=1 << 23, per_event_counts=1)
     ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
     layer_parity(wl, r["edep"], ref["edep"])
     assert np.abs(_conservation(wl, r)).max() < 1e-5
     c = r["counters"]
-    _report("config4_integral", events=wl.n_events, kernel_ms=r["kernel_ms"],
+    _report("e-10GeV_PbPS50_integral", events=wl.n_events, kernel_ms=r["kernel_ms"],
             events_per_s=wl.n_events / (r["kernel_ms"] / 1e3), steps=c["steps"], discrete=c["discrete"],
             layers=_layer_stats(wl, r["edep"], ref["edep"]))

@@ -63,7 +63,7 @@ def layer_parity(wl, g_edep, o_edep, frac=0.01, rel=0.005):
     return pull.max(), big.sum()
 
 
-# ---------------------------------------------------------------- photon slab (config 1)
+# ---------------------------------------------------------------- photon slab
 @pytest.mark.parametrize("prec", [0, 1], ids=["mixed", "fp64"])
 def test_photon_slab_transmission(gvmod, oracle_mod, prec):
     wl = W.photon_slab(100_000)
@@ -131,7 +131,7 @@ def test_energy_and_charge_conservation_mixed(gvmod):
 # ---------------------------------------------------------------- full-size workloads
 def test_full_size_pbps_10GeV_matches_oracle(gvmod, oracle_mod):
     """The benchmark workload (2000 x 10 GeV e-) in the benchmark launch shape."""
-    wl = W.config(4)
+    wl = W.standard(W.PBPS_10GEV)
     ctx = _ctx(gvmod, wl, stack_capacity=1 << 23)
     r = ctx.transport()
     assert r["status"] == 0
@@ -142,8 +142,8 @@ def test_full_size_pbps_10GeV_matches_oracle(gvmod, oracle_mod):
     assert abs(tot - (_T0(wl).sum() + 2 * ME * (c["n_annih"] - c["n_pair"]))) < 1e-6 * _T0(wl).sum()
 
 
-def test_mixed_types_config3(gvmod, oracle_mod):
-    wl = W.config(3)
+def test_mixed_types_pbps(gvmod, oracle_mod):
+    wl = W.standard(W.PBPS_MIXED)
     ctx = _ctx(gvmod, wl, stack_capacity=1 << 23)
     r = ctx.transport()
     assert r["status"] == 0

@@ -58,7 +58,7 @@ def _layer_stats(wl, g_edep, o_edep):
 
 def test_precision_study_10GeV(gvmod, oracle_mod):
     """2000 x 10 GeV e- on Pb/polystyrene: FP64 GPU, mixed GPU and the oracle."""
-    wl = W.config(4)
+    wl = W.standard(W.PBPS_10GEV)
     ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
     o_res = (ref["edep"].sum(1) + ref["escape"]
              - (_T0(wl) + 2 * ME * (ref["counts"][:, 8] - ref["counts"][:, 7]))) / _T0(wl)
@@ -78,34 +78,34 @@ def test_precision_study_10GeV(gvmod, oracle_mod):
     _report("precision_10GeV_PbPS", **out)
 
 
-def test_config2_1GeV(gvmod, oracle_mod):
-    wl = W.config(2)
+def test_pbps_1GeV_measured(gvmod, oracle_mod):
+    wl = W.standard(W.PBPS_1GEV)
     r = _run(gvmod, wl)
     ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
     layer_parity(wl, r["edep"], ref["edep"])
     c = r["counters"]
-    _report("config2_1GeV_PbPS", events=wl.n_events, kernel_ms=r["kernel_ms"],
+    _report("e-1GeV_PbPS50", events=wl.n_events, kernel_ms=r["kernel_ms"],
             events_per_s=wl.n_events / (r["kernel_ms"] / 1e3), steps_per_s=c["steps"] / (r["kernel_ms"] / 1e3),
             layers=_layer_stats(wl, r["edep"], ref["edep"]))
 
 
-def test_config3_mixed_types_measured(gvmod):
-    wl = W.config(3)
+def test_pbps_mixed_types_measured(gvmod):
+    wl = W.standard(W.PBPS_MIXED)
     r = _run(gvmod, wl, stack_capacity=1 << 23)
     c = r["counters"]
     T0 = _T0(wl).sum()
     tot = r["edep"].sum() + r["escape"].sum()
     assert abs(tot - (T0 + 2 * ME * (c["n_annih"] - c["n_pair"]))) < 1e-6 * T0
-    _report("config3_mixed_types", events=wl.n_events, kernel_ms=r["kernel_ms"],
+    _report("mixed_PbPS50", events=wl.n_events, kernel_ms=r["kernel_ms"],
             events_per_s=wl.n_events / (r["kernel_ms"] / 1e3), steps_per_s=c["steps"] / (r["kernel_ms"] / 1e3),
             idle_lane_frac=1.0 - c["steps"] / max(c["lane_slots"], 1), live_peak=c["live_peak"],
             generations=c["generations"], launches=r["launches"])
 
 
-def test_config5_full_size(gvmod, oracle_mod):
+def test_wsi_100GeV_cells_full_size(gvmod, oracle_mod):
     """1e4 x 100 GeV e- on W/Si with 32x32 cells: the whole run on the GPU,
     the oracle on the first 1000 events."""
-    wl = W.config(5)
+    wl = W.standard(W.WSI_100GEV)
     cap = 1 << 23
     r = _run(gvmod, wl, stack_capacity=cap)
     c = r["counters"]
@@ -118,7 +118,7 @@ def test_config5_full_size(gvmod, oracle_mod):
     sub = wl.subset(1000)
     ref = oracle_mod.Oracle(sub).transport(n_threads=NTHR)
     layer_parity(sub, r["edep"][:1000], ref["edep"])
-    _report("config5_WSi_cells_100GeV", events=wl.n_events, kernel_ms=r["kernel_ms"],
+    _report("e-100GeV_WSi50_cells", events=wl.n_events, kernel_ms=r["kernel_ms"],
             events_per_s=wl.n_events / (r["kernel_ms"] / 1e3), steps_per_s=c["steps"] / (r["kernel_ms"] / 1e3),
             steps=c["steps"], live_peak=c["live_peak"], capacity=cap, generations=c["generations"],
             layers_first1000=_layer_stats(sub, r["edep"][:1000], ref["edep"]))

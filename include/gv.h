@@ -32,6 +32,7 @@ extern "C" {
 #define GV_ERR_TIMEOUT -5    /* generation budget exhausted before all tracks ended */
 #define GV_ERR_NUMERIC -6    /* a track reached a non-finite energy or position */
 #define GV_ERR_CUDA -7       /* a CUDA runtime call failed */
+#define GV_ERR_INTERNAL -8   /* an index or state check failed (library built with GV_CHECKS) */
 
 #define GV_MAX_ELEM 4
 #define GV_MAX_MAT 4

@@ -29,7 +29,8 @@ def _needs(out: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src: str, verbose: bool, min_blocks: int = 0, max_block: int = 0, maxnreg: int = 0) -> str:
+def _compile(src: str, verbose: bool, min_blocks: int = 0, max_block: int = 0, maxnreg: int = 0,
+             checks: bool = False) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     deps = [os.path.join(CSRC, src)] + [os.path.join(CSRC, h) for h in HEADERS] + \
         [os.path.join(ROOT, "include", "gv.h")]
@@ -46,6 +47,8 @@ def _compile(src: str, verbose: bool, min_blocks: int = 0, max_block: int = 0, m
             cmd.insert(1, f"-DGV_MAX_BLOCK={int(max_block)}")
         if maxnreg:
             cmd.insert(1, f"-DGV_MAXNREG={int(maxnreg)}")
+        if checks:
+            cmd.insert(1, "-DGV_CHECKS")
     else:
         cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-c",
                os.path.join(CSRC, src), "-o", obj]
@@ -54,15 +57,16 @@ def _compile(src: str, verbose: bool, min_blocks: int = 0, max_block: int = 0, m
 
 
 def build(force: bool = False, verbose: bool = False, min_blocks: int = 0, out: str = OUT,
-          max_block: int = 0, maxnreg: int = 0) -> str:
+          max_block: int = 0, maxnreg: int = 0, checks: bool = False) -> str:
     """Compile libgv.so.  min_blocks > 0 builds the step kernel with a register
     budget for that many resident blocks per SM of max_block threads (default
     256, the largest block_size it then accepts); maxnreg > 0 caps its
-    registers per thread directly instead.  Such variants go to their own build
+    registers per thread directly instead; checks=True compiles the index and
+    state checks (GV_CHECKS) in.  Such variants go to their own build
     directory (pass `out` to keep the default library)."""
     global BUILD
-    variant = min_blocks or max_block or maxnreg
-    build_dir = BUILD if not variant else BUILD + f"_mb{min_blocks}_{max_block}_{maxnreg}"
+    variant = min_blocks or max_block or maxnreg or checks
+    build_dir = BUILD if not variant else BUILD + f"_mb{min_blocks}_{max_block}_{maxnreg}_{int(checks)}"
     os.makedirs(build_dir, exist_ok=True)
     if force:
         for f in os.listdir(build_dir):
@@ -70,7 +74,7 @@ def build(force: bool = False, verbose: bool = False, min_blocks: int = 0, out: 
     saved, BUILD = BUILD, build_dir
     try:
         with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-            objs = list(ex.map(lambda s: _compile(s, verbose, min_blocks, max_block, maxnreg), SOURCES))
+            objs = list(ex.map(lambda s: _compile(s, verbose, min_blocks, max_block, maxnreg, checks), SOURCES))
     finally:
         BUILD = saved
     if force or _needs(out, objs):

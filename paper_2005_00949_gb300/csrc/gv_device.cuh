@@ -59,6 +59,21 @@ template <> __device__ __forceinline__ double r_inf<double>() { return __longlon
 
 template <typename R> struct alignas(4 * sizeof(R)) V4 { R x, y, z, w; };
 
+// Index and state checks of the checking build (-DGV_CHECKS): a failed check
+// records GV_ERR_INTERNAL in the status word it is given (if any) and the
+// work goes on with clamped values; nothing traps.  The release build
+// compiles them away.
+#ifdef GV_CHECKS
+#define GV_CHECK(status_ptr, cond)                                          \
+  do {                                                                      \
+    if (!(cond) && (status_ptr)) atomicCAS((status_ptr), 0, GV_ERR_INTERNAL); \
+  } while (0)
+#else
+#define GV_CHECK(status_ptr, cond) \
+  do {                             \
+  } while (0)
+#endif
+
 // one bin of an alias table: acceptance q, alias index, pdf at the bin edges
 template <typename R> struct AliasBin { float q; int a; R p0, p1; };
 
@@ -100,6 +115,7 @@ template <typename R> struct View {
   const unsigned char *smat; // material of each sub-slab
   const AliasBin<R> *bins;   // all models, [off + ie*kNB + j]
   const R *smax;             // integral approach bound [(mat*2 + type-1)*kGridN + node], smem or global
+  int *status;               // where checks record a failure (checking build), or null
   ModelMeta meta[kNModel];
   GeoConst geo;
   CutConst cut;
@@ -175,6 +191,7 @@ template <typename R> __device__ __forceinline__ V4<R> lerp4(const V4<R> &a, con
 
 template <typename R>
 __device__ __forceinline__ V4<R> lookup_at(const View<R> &V, int mat, int type, int i, R f) {
+  GV_CHECK(V.status, i >= 0 && i <= kGridN - 2 && mat >= 0 && mat < GV_MAX_MAT && type >= 0 && type <= 2);
   const V4<R> *t = V.xs + (mat * 3 + type) * kGridN;
   return lerp4(t[i], t[i + 1], f);
 }
@@ -312,10 +329,12 @@ __device__ R alias_sample(const View<R> &V, int m, R E, R ug, R ub, R ui, R *xi_
   int j = static_cast<int>(x);
   j = j > kNB - 1 ? kNB - 1 : (j < 0 ? 0 : j);
   const R fr = x - static_cast<R>(j);
+  GV_CHECK(V.status, ie >= 0 && ie < M.nE);
   const AliasBin<R> *row = V.bins + M.off + ie * kNB;
   AliasBin<R> b = row[j];
   int bin = j;
   if (!(fr < static_cast<R>(b.q))) {
+    GV_CHECK(V.status, b.a >= 0 && b.a < kNB);
     bin = b.a;
     b = row[bin];
   }
@@ -334,6 +353,7 @@ __device__ R alias_sample(const View<R> &V, int m, R E, R ug, R ub, R ui, R *xi_
 template <typename R>
 __device__ __forceinline__ R distance(const View<R> &V, double x, double y, double z, R u, R v, R w, int sub,
                                       int &next, int &plane) {
+  GV_CHECK(V.status, sub >= 0 && sub < V.geo.nsub);
   R d = r_inf<R>();
   int nx = sub, pl = -1;
   if (w != R(0)) {

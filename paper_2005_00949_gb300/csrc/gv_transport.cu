@@ -53,6 +53,7 @@ template <typename R>
 __device__ __forceinline__ void deposit(const View<R> &V, const DevState<R> *S, unsigned ev, int sub, double px,
                                         double py, R dE, Pending<R> *pd = nullptr) {
   if (!(dE != R(0)) || sub < 0) return;
+  GV_CHECK(&S->ctl->status, ev < S->n_events && sub < V.geo.nsub);
   const unsigned long long key = static_cast<unsigned long long>(ev) * V.geo.nsub + sub;
   if (pd) {
     if (pd->key == key) {
@@ -709,6 +710,7 @@ __global__ void GV_STEP_BOUNDS
         t.flags = sf >> 16;
         t.type = qsel;
         alive = true;
+        GV_CHECK(&ctl->status, t.sub >= 0 && t.sub < V.geo.nsub && t.ev < S->n_events && t.E >= R(0));
       }
     } else if (idx < n_prim_gen) {
       const unsigned i = s_pb + idx;
@@ -1025,6 +1027,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_ALONG_MIN_BLOCKS : 2)
         t.flags = sf >> 16;
         t.type = qsel;
         alive = true;
+        GV_CHECK(&ctl->status, t.sub >= 0 && t.sub < V.geo.nsub && t.ev < S->n_events && t.E >= R(0));
       }
     } else if (idx < n_prim_gen) {
       const unsigned i = s_pb + idx;
@@ -1402,6 +1405,7 @@ template <typename R> View<R> make_view(const Ctx *c) {
   v.smat = c->d_smat;
   v.bins = reinterpret_cast<const AliasBin<R> *>(c->d_bins);
   v.smax = reinterpret_cast<const R *>(c->d_smax);
+  v.status = nullptr;  // unit kernels: no status word
   for (int m = 0; m < kNModel; ++m) v.meta[m] = c->meta[m];
   v.geo.nsub = c->nsub;
   v.geo.nsub_layer = c->geo.n_sub;
@@ -1505,6 +1509,7 @@ template <typename R> DevState<R> make_state(Ctx *c) {
     for (int q = 0; q < 3; ++q) s.q[par][q] = carve<R>(p, c->cfg.stack_capacity);
   s.capacity = static_cast<unsigned long long>(c->cfg.stack_capacity);
   s.ctl = c->d_ctl;
+  s.view.status = &c->d_ctl->status;  // device address; checks of the checking build
   s.block_size = c->cfg.block_size;
   s.chunk = (c->cfg.pipeline || c->cfg.process_sort || c->cfg.claim_chunks == 0) ? c->cfg.block_size : 32;
   s.claim_chunks = c->cfg.claim_chunks;
@@ -1890,6 +1895,7 @@ const char *gv_strerror(int code) {
     case GV_ERR_TIMEOUT: return "generation budget exhausted";
     case GV_ERR_NUMERIC: return "non-finite track state";
     case GV_ERR_CUDA: return "CUDA runtime error";
+    case GV_ERR_INTERNAL: return "internal check failed";
     default: return "unknown error";
   }
 }
@@ -2039,6 +2045,7 @@ extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long 
     for (int q = 0; q < 3; ++q) s.q[par][q] = carve_static(qp);
   s.capacity = static_cast<unsigned long long>(kStaticCap);
   s.ctl = reinterpret_cast<Ctl *>(base + kStaticCtlOff);
+  s.view.status = &s.ctl->status;
   s.mode = GV_BATCHED;
   s.chunk = c->cfg.block_size;  // the non-basketizing kernel, one claim per block
   s.claim_chunks = 0;

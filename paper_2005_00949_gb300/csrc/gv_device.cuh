@@ -34,6 +34,10 @@ __device__ __forceinline__ double m_floor(double x) { return floor(x); }
 // callers keep the divisor away from 0 and from the top of the range.
 __device__ __forceinline__ float q_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double q_div(double a, double b) { return a / b; }
+// 1/sqrt(x): the hardware reciprocal square root in FP32 (the same 2-ulp
+// class as q_div), the IEEE quotient in FP64.
+__device__ __forceinline__ float q_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double q_rsqrt(double x) { return 1.0 / sqrt(x); }
 
 // log(1 + x) for |x| <= 0.16 in FP32: its Taylor series to x^8 (truncation
 // error below 8e-9 there, under half an FP32 ulp of the result).
@@ -249,13 +253,13 @@ template <typename R> __device__ __forceinline__ R reduced_to_physical(int m, R 
       const R a = static_cast<R>(kME) / E;
       return a + xi * (R(1) - R(2) * a);
     }
-    case kBrem: return cut * m_exp(xi * m_log(E / cut));
+    case kBrem: return cut * m_exp(xi * m_log(q_div(E, cut)));
     case kMoller: {
-      const R x = cut / E;
-      return x * m_exp(xi * m_log(R(0.5) / x));
+      const R x = q_div(cut, E);
+      return x * m_exp(xi * m_log(q_div(R(0.5), x)));
     }
     case kBhabha: {
-      const R x = cut / E;
+      const R x = q_div(cut, E);
       return x * m_exp(-xi * m_log(x));
     }
     default: {  // softer annihilation photon, eps_min = 1/((g+1)(1+s)), s = sqrt((g-1)/(g+1))
@@ -339,7 +343,7 @@ __device__ R alias_sample(const View<R> &V, int m, R E, R ug, R ub, R ui, R *xi_
     b = row[bin];
   }
   const R p0 = b.p0, p1 = b.p1;
-  const R t = ui * (p0 + p1) / (p0 + m_sqrt(p0 * p0 + ui * (p1 * p1 - p0 * p0)));
+  const R t = q_div(ui * (p0 + p1), p0 + m_sqrt(p0 * p0 + ui * (p1 * p1 - p0 * p0)));
   const R xi = (static_cast<R>(bin) + t) * static_cast<R>(1.0 / kNB);
   if (xi_out) *xi_out = xi;
   return reduced_to_physical<R>(m, E, xi, V.rc.cut[m]);
@@ -417,9 +421,10 @@ __device__ __forceinline__ void rotate(const R d[3], R ct, R st, R cp, R sp, R o
   const R lx = st * cp, ly = st * sp, lz = ct;
   R up = d[0] * d[0] + d[1] * d[1];
   if (up > R(0)) {
-    up = m_sqrt(up);
-    o[0] = (d[0] * d[2] * lx - d[1] * ly) / up + d[0] * lz;
-    o[1] = (d[1] * d[2] * lx + d[0] * ly) / up + d[1] * lz;
+    const R iu = q_rsqrt(up);
+    up = up * iu;
+    o[0] = (d[0] * d[2] * lx - d[1] * ly) * iu + d[0] * lz;
+    o[1] = (d[1] * d[2] * lx + d[0] * ly) * iu + d[1] * lz;
     o[2] = -up * lx + d[2] * lz;
   } else if (d[2] < R(0)) {
     o[0] = -lx; o[1] = ly; o[2] = -lz;
@@ -436,7 +441,7 @@ __device__ __forceinline__ void rotate_vec(const R d[3], R along, R perp, R cp, 
     o[0] = d[0]; o[1] = d[1]; o[2] = d[2];
     return;
   }
-  const R inv = R(1) / m_sqrt(n2);
+  const R inv = q_rsqrt(n2);
   rotate(d, along * inv, perp * inv, cp, sp, o);
 }
 
@@ -621,13 +626,14 @@ __device__ int interact(const View<R> &V, int type, int p, R &E, R d[3], const R
   R sp, cp;
   m_sincos(static_cast<R>(2.0 * kPi) * u[5], &sp, &cp);
   if (model == kCompton) {  // eps = eps0^(1-xi)
-    const R k = E, kap = k / ME;
+    const R k = E, kap = k * static_cast<R>(1.0 / kME);
     const R L0 = -m_log1p(R(2) * kap);
     const R a = (R(1) - xi) * L0;
     const R eps = m_exp(a);
     const R om_eps = -m_expm1(a);                   // 1 - eps
-    const R omc = om_eps / (kap * eps);             // 1 - cos(theta)
-    const R opc = m_expm1(-xi * L0) / (kap * eps);  // 1 + cos(theta)
+    const R ike = q_div(R(1), kap * eps);
+    const R omc = om_eps * ike;                // 1 - cos(theta)
+    const R opc = m_expm1(-xi * L0) * ike;     // 1 + cos(theta)
     const R st = m_sqrt(omc * opc);
     const R ct = omc < R(1) ? R(1) - omc : opc - R(1);
     R d1[3], de[3];
@@ -654,7 +660,7 @@ __device__ int interact(const View<R> &V, int type, int p, R &E, R d[3], const R
     Tm = Tm < R(0) ? R(0) : Tm;
     Tp = Tp < R(0) ? R(0) : Tp;
     R st, ct;
-    m_sincos(ME / k, &st, &ct);
+    m_sincos(q_div(ME, k), &st, &ct);
     R dm[3], dp[3];
     rotate(d, ct, st, cp, sp, dm);
     rotate(d, ct, st, -cp, -sp, dp);
@@ -673,18 +679,19 @@ __device__ int interact(const View<R> &V, int type, int p, R &E, R d[3], const R
   R T = E;
   if (model == kBrem) {
     R st, ct, dg[3];
-    m_sincos(ME / (T + ME), &st, &ct);
+    m_sincos(q_div(ME, T + ME), &st, &ct);
     rotate(d, ct, st, cp, sp, dg);
     if (v >= tcut) add_kid(kids, 0, v, dg);
     else local += v;
     T -= v;
   } else if (model != kAnnih) {  // ionisation: Moller eps = xc (1/(2xc))^xi, Bhabha eps = xc^(1-xi)
     const R eps = v;
-    const R om_eps = model == kMoller ? R(1) - eps : -m_expm1((R(1) - xi) * m_log(ec / T));
+    const R om_eps = model == kMoller ? R(1) - eps : -m_expm1((R(1) - xi) * m_log(q_div(ec, T)));
     const R Td = eps * T;
     const R den = eps * T + R(2) * ME;
     // delta ray: cos^2 = eps (T + 2m) / (eps T + 2m), sin^2 = 2m (1 - eps) / (eps T + 2m)
-    const R ct = m_sqrt(eps * (T + R(2) * ME) / den), st = m_sqrt(R(2) * ME * om_eps / den);
+    const R iden = q_div(R(1), den);
+    const R ct = m_sqrt(eps * (T + R(2) * ME) * iden), st = m_sqrt(R(2) * ME * om_eps * iden);
     R dd[3], dn[3];
     rotate(d, ct, st, cp, sp, dd);
     // primary: p' = p (1 - eps) along d, sqrt(2 m T eps (1 - eps)) across

@@ -293,3 +293,32 @@ def test_resuming_an_event_range_reproduces_it(gvmod):
     assert np.all(tail["counts"][:180] == 0)
     scale = np.maximum(full["edep"][180:].sum(1, keepdims=True), 1.0)
     assert (np.abs(tail["edep"][180:] - full["edep"][180:]) / scale).max() < 1e-9
+
+
+# ---------------------------------------------------------------- maximum sizes
+def test_largest_geometry_and_material_set(gvmod, oracle_mod):
+    """The largest geometry the ABI takes: 4 materials, 8 sub-slabs per
+    layer, 128 layers = 1024 sub-slabs (GV_MAX_MAT, GV_MAX_SUB,
+    GV_MAX_SUBTOTAL), with cells; FP64 event by event and mixed per-layer
+    means against the oracle."""
+    mats = [W.LEAD, W.LIQUID_ARGON, W.TUNGSTEN, W.POLYSTYRENE]
+    thick = [0.05, 0.1, 0.03, 0.12, 0.02, 0.2, 0.04, 0.08]
+    p = W.make_primaries(400)
+    p["type"] = np.arange(400) % 3
+    p["E"] = 500.0
+    p["w"] = 1.0
+    p["event"] = np.arange(400)
+    wl = W.Workload(name="max_geometry", materials=mats, n_layers=128, sub_thick=thick,
+                    sub_mat=[0, 1, 2, 3, 0, 1, 2, 3], half_x=10.0, half_y=10.0, nx=8, ny=8,
+                    gamma_cut=0.2, e_cut=0.5, track_cut=1e-3, process_mask=W.P_ALL, primaries=p,
+                    n_events=400)
+    assert wl.n_subtotal == 1024
+    ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
+    r64 = _ctx(gvmod, wl, precision=1, per_event_counts=1).transport(per_event=True)
+    same = np.all(r64["counts"][:, :11] == ref["counts"][:, :11], axis=1)
+    assert same.mean() >= 0.9, same.mean()
+    assert np.abs(r64["edep"][same] - ref["edep"][same]).max() < 1e-9 * 500.0
+    r32 = _ctx(gvmod, wl).transport()
+    assert r32["status"] == 0
+    layer_parity(wl, r32["edep"], ref["edep"])
+    assert np.allclose(r32["cell"].sum((1, 2)), r32["edep"].reshape(400, 128, 8).sum((0, 2)), rtol=1e-9)

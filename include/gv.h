@@ -158,6 +158,10 @@ typedef struct {
                                  along-step kernel hands the tracks due a discrete interaction to
                                  an interaction kernel that runs each warp on one (type, process)
                                  key (needs scoring = 0; stack_capacity requests per generation) */
+  int local_stack;            /* 1 (default): with several rounds per claim, the basketizing kernel keeps the
+                                 secondaries a block makes in a shared-memory stack and gives them to
+                                 its idle lanes in the following rounds (the StackBuffer, Sec. 2.1.2)
+                                 instead of leaving them to the next generation */
 } gv_config;
 
 /* A primary track; layout shared with the seeded input generator.  Its random

@@ -29,6 +29,7 @@ SPACE = {
     "claim_chunks": [0, 1],
     "along_steps": [2, 3, 4, 6],
     "scoring": [0, 1],
+    "local_stack": [1, 0],
     "block_size": [128, 256],
     "blocks_per_sm": [2, 3, 4],
     "steps_per_claim": [1, 2, 3, 4],

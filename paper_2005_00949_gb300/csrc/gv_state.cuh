@@ -100,6 +100,8 @@ template <typename R> struct DevState {
   unsigned xs_bytes, zb_bytes;  // staged into shared memory
   unsigned smem_req_off;        // start of the basketizer's request records
   unsigned smax_off, smax_bytes; // the integral approach's bound, staged into shared memory
+  unsigned smem_lk_off;          // the block's secondary stack (local_stack)
+  int local_stack;
 };
 
 }  // namespace gv

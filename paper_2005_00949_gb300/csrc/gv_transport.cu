@@ -401,11 +401,32 @@ template <typename R> __device__ __forceinline__ Parent parent_of(const Trk<R> &
   return p;
 }
 
-// PostStepActions: append the step's secondaries to the output queues.  Called by all 32
-// lanes of a converged warp (lanes without secondaries pass kids.n == 0).
+// A secondary kept in the block's shared-memory stack (the StackBuffer of
+// Sec. 2.1.2 for one block): its lanes take it up in a later round of the
+// same claim instead of leaving it to the next generation.
+template <typename R> struct LKid {
+  double x, y, z;
+  unsigned long long id;
+  R u, v, w, E;
+  unsigned ev;
+  int sub, type;
+};
+
+// The block's secondary stack: `top` entries (it may run past `cap` while
+// appends overflow to the global queues, and below 0 while empty lanes try
+// to pop; both are only ever read through the bounds below).
+template <typename R> struct LocalStack {
+  LKid<R> *e;
+  int *top;
+  int cap;
+};
+
+// PostStepActions: append the step's secondaries to the output queues, or,
+// with a local stack, to the block's stack while it has room.  Called by all
+// 32 lanes of a converged warp (lanes without secondaries pass kids.n == 0).
 template <typename R>
 __device__ void push_kids(const DevState<R> *S, int out, const Parent &t, const Kids<R> &kids, uint32_t kk,
-                          BlockCnt *bc) {
+                          BlockCnt *bc, const LocalStack<R> *ls = nullptr) {
   const unsigned any = __ballot_sync(0xffffffffu, kids.n > 0);
   if (!any) return;
   uint32_t w[6] = {0, 0, 0, 0, 0, 0};
@@ -420,11 +441,33 @@ __device__ void push_kids(const DevState<R> *S, int out, const Parent &t, const 
       w[4] = b.x; w[5] = b.y;
     }
   }
+  // the block's stack first, while it has room (the ids above keep each
+  // kid's index in the list, so where it goes changes no result)
+  unsigned local = 0;  // bit j: kid j went to the block's stack
+  if (ls) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      if (j >= kids.n) continue;
+      const int slot = atomicAdd(ls->top, 1);
+      if (slot < 0 || slot >= ls->cap) continue;
+      LKid<R> &e = ls->e[slot];
+      e.x = t.x; e.y = t.y; e.z = t.z;
+      e.id = static_cast<unsigned long long>(w[2 * j]) | (static_cast<unsigned long long>(w[2 * j + 1]) << 32);
+      e.u = kids.d[j][0]; e.v = kids.d[j][1]; e.w = kids.d[j][2];
+      e.E = kids.E[j];
+      e.ev = t.ev;
+      e.sub = t.sub;
+      e.type = kids.type[j];
+      atomicAdd(&bc->c[GV_C_TRK_G + kids.type[j]], 1ull);
+      if (S->evcnt) atomicAdd(&S->evcnt[static_cast<size_t>(t.ev) * GV_NCOUNT + GV_C_TRK_G + kids.type[j]], 1ull);
+      local |= 1u << j;
+    }
+  }
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     unsigned c = 0;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) c += (j < kids.n && kids.type[j] == q) ? 1u : 0u;
+    for (int j = 0; j < 3; ++j) c += (j < kids.n && kids.type[j] == q && !(local >> j & 1u)) ? 1u : 0u;
     if (!__ballot_sync(0xffffffffu, c > 0)) continue;
     unsigned total;
     unsigned slot = warp_reserve(&S->ctl->cnt[out][q], c, total);
@@ -436,7 +479,7 @@ __device__ void push_kids(const DevState<R> *S, int out, const Parent &t, const 
     }
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      if (!(j < kids.n && kids.type[j] == q)) continue;
+      if (!(j < kids.n && kids.type[j] == q) || (local >> j & 1u)) continue;
       const unsigned long long id = static_cast<unsigned long long>(w[2 * j]) |
                                     (static_cast<unsigned long long>(w[2 * j + 1]) << 32);
       store(S->q[out][q], slot, t.x, t.y, t.z, kids.d[j][0], kids.d[j][1], kids.d[j][2], kids.E[j], R(-1), id, t.ev,
@@ -481,6 +524,25 @@ __device__ __forceinline__ void push_survivor(const DevState<R> *S, int out, con
     }
     store(S->q[out][q], slot, t.x, t.y, t.z, t.u, t.v, t.w, t.E, t.nlam, t.id, t.ev, t.step,
           t.sub | (t.flags << 16));
+  }
+}
+
+// A block-stack secondary written to the output queue (e == nullptr:
+// nothing).  All 32 lanes of a converged warp.
+template <typename R> __device__ __forceinline__ void push_lkid(const DevState<R> *S, int out, const LKid<R> *e) {
+  const int type = e ? e->type : -1;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const bool mine = type == q;
+    if (!__ballot_sync(0xffffffffu, mine)) continue;
+    unsigned total;
+    const unsigned slot = warp_reserve(&S->ctl->cnt[out][q], mine ? 1u : 0u, total);
+    if (!mine) continue;
+    if (slot >= S->capacity) {
+      set_status(S->ctl, GV_ERR_STACK_FULL);
+      continue;
+    }
+    store(S->q[out][q], slot, e->x, e->y, e->z, e->u, e->v, e->w, e->E, R(-1), e->id, e->ev, 0u, e->sub);
   }
 }
 
@@ -600,6 +662,7 @@ __global__ void GV_STEP_BOUNDS
   __shared__ unsigned s_chunk, s_end[4], s_pb;
   __shared__ unsigned s_slice[kNClaim + 1];
   __shared__ int s_K, s_last;
+  __shared__ int s_ltop;  // the block's secondary stack (local_stack)
   __shared__ unsigned s_wcnt[SORT ? kNKey : 1][SORT ? 16 : 1];
   __shared__ unsigned s_walive[SORT ? 16 : 1];
   Ctl *ctl = S->ctl;
@@ -635,6 +698,7 @@ __global__ void GV_STEP_BOUNDS
         s_slice[r] = static_cast<unsigned>((static_cast<unsigned long long>(s_end[3]) * r) / kNClaim);
       s_pb = ctl->prim_begin;
       s_K = ctl->K;
+      s_ltop = 0;
     }
     if (tid < 16) bc.c[tid] = 0;
   }
@@ -644,6 +708,13 @@ __global__ void GV_STEP_BOUNDS
   const unsigned cap = static_cast<unsigned>(S->capacity);
   const unsigned n_in[3] = {min(ctl->cnt[in][0], cap), min(ctl->cnt[in][1], cap), min(ctl->cnt[in][2], cap)};
   const unsigned n_prim_gen = ctl->prim_count;
+  // With several rounds per claim, the secondaries made in a round stay in
+  // the block and fill its idle lanes in the next rounds (local_stack).
+  const bool use_local = SORT && S->local_stack && s_K > 1;
+  LocalStack<R> lstk;
+  lstk.e = reinterpret_cast<LKid<R> *>(smem + S->smem_lk_off);
+  lstk.top = &s_ltop;
+  lstk.cap = static_cast<int>(blockDim.x);
   int w_slice = 0;
   {
     unsigned smid;
@@ -747,6 +818,23 @@ __global__ void GV_STEP_BOUNDS
       // (with the basketizer the block leaves the loop together, after the
       // count barrier below shows that no lane was alive)
       if (!SORT && !__any_sync(0xffffffffu, alive)) break;
+      if (use_local && kk > 0 && !alive) {  // take up a secondary of an earlier round
+        const int i = atomicSub(&s_ltop, 1) - 1;
+        if (i >= 0 && i < lstk.cap) {
+          const LKid<R> &e = lstk.e[i];
+          t.x = e.x; t.y = e.y; t.z = e.z;
+          t.u = e.u; t.v = e.v; t.w = e.w;
+          t.E = e.E;
+          t.nlam = R(-1);
+          t.id = e.id;
+          t.ev = e.ev;
+          t.step = 0;
+          t.sub = e.sub;
+          t.flags = 0;
+          t.type = e.type;
+          alive = true;
+        }
+      }
       const bool was_alive = alive;
       Kids<R> kids;
       kids.n = 0;
@@ -824,6 +912,7 @@ __global__ void GV_STEP_BOUNDS
         const unsigned ma = __ballot_sync(0xffffffffu, was_alive);
         if (lane == 0) s_walive[warp] = ma;
         __syncthreads();
+        if (use_local && tid == 0 && s_ltop < 0) s_ltop = 0;  // pops of an empty stack
         unsigned any = 0;
         for (int w = 0; w < nw; ++w) any |= s_walive[w];
         if (!any) break;  // uniform: no lane of the block was alive this step
@@ -878,7 +967,7 @@ __global__ void GV_STEP_BOUNDS
           q.E = e; q.d0 = d[0]; q.d1 = d[1]; q.d2 = d[2];
           q.tp = r;
         }
-        push_kids(S, out, par, kb, pk, &bc);
+        push_kids(S, out, par, kb, pk, &bc, use_local ? &lstk : nullptr);
         __syncthreads();
         if (key >= 0) {
           const IReq<R> &q = req[slot];
@@ -893,6 +982,16 @@ __global__ void GV_STEP_BOUNDS
     }
     if (MERGE) warp_flush(S, pend);  // nothing stays pending past a claim
     push_survivor(S, out, t, alive);
+    if (use_local) {  // what is left on the block's stack goes to the next generation
+      __syncthreads();
+      const int n = max(0, min(s_ltop, lstk.cap));
+      for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + tid;
+        push_lkid(S, out, i < n ? &lstk.e[i] : static_cast<const LKid<R> *>(nullptr));
+      }
+      __syncthreads();
+      if (tid == 0) s_ltop = 0;
+    }
   }
   // flush block counters; the last block plans the next generation
   __syncthreads();
@@ -1239,6 +1338,7 @@ struct Ctx {
   int last_status = 0;
   ModelMeta meta[kNModel];
   size_t xs_bytes = 0, zb_bytes = 0, smem_bytes = 0, req_off = 0, bins_bytes = 0, smax_bytes = 0, smax_off = 0;
+  size_t lk_off = 0;
   int grid = 0, grid_b = 0;
   // split pipeline: interaction requests and their per-key index lists
   void *d_req = nullptr;
@@ -1294,6 +1394,7 @@ int validate_cfg(const gv_config &c) {
   if (c.along_steps < 1 || c.along_steps > 64) return GV_ERR_BAD_ARG;
   if (c.scoring < 0 || c.scoring > 1) return GV_ERR_BAD_ARG;
   if (c.l2_persist < 0 || c.l2_persist > 1) return GV_ERR_BAD_ARG;
+  if (c.local_stack < 0 || c.local_stack > 1) return GV_ERR_BAD_ARG;
   if (c.pipeline < 0 || c.pipeline > 1 || (c.pipeline == 1 && c.scoring != 0)) return GV_ERR_BAD_ARG;
   return GV_OK;
 }
@@ -1491,6 +1592,8 @@ template <typename R> int prepare_device(Ctx *c) {
     return GV_OK;
   }
   c->smem_bytes = c->req_off + (c->cfg.process_sort ? sizeof(IReq<R>) * c->cfg.block_size : 0);
+  c->lk_off = (c->smem_bytes + 15) / 16 * 16;
+  if (c->cfg.process_sort && c->cfg.local_stack) c->smem_bytes = c->lk_off + sizeof(LKid<R>) * c->cfg.block_size;
   const void *kern = reinterpret_cast<const void *>(pick_step_kernel<R>(c->cfg, c->geo.field_T != 0.0));
   CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(c->smem_bytes)));
   int occ = 0;
@@ -1531,6 +1634,8 @@ template <typename R> DevState<R> make_state(Ctx *c) {
   s.zb_bytes = static_cast<unsigned>(c->zb_bytes);
   s.smem_req_off = static_cast<unsigned>(c->req_off);
   s.smax_off = static_cast<unsigned>(c->smax_off);
+  s.smem_lk_off = static_cast<unsigned>(c->lk_off);
+  s.local_stack = c->cfg.local_stack;
   s.smax_bytes = static_cast<unsigned>(c->smax_bytes);
   return s;
 }
@@ -1753,6 +1858,7 @@ int gv_default_config(gv_config *cfg) {
   cfg->scoring = 0;
   cfg->l2_persist = 0;
   cfg->pipeline = 0;
+  cfg->local_stack = 1;
   return GV_OK;
 }
 

@@ -24,6 +24,7 @@ def _cases():
         ("mixed_fp64", mixed, {"precision": 1}),
         ("nosort", mixed, {"process_sort": 0, "claim_chunks": 1}),
         ("merged_scoring", mixed, {"scoring": 1}),
+        ("local_stack", mixed, {"local_stack": 1, "tail_steps_per_claim": 8}),
         ("split", mixed, {"pipeline": 1}),
         ("one_event", mixed, {"mode": 1}),
         ("msc_field", em3, {}),

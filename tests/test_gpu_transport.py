@@ -185,7 +185,9 @@ def test_integer_counts_invariant_to_launch_shape(gvmod):
               dict(process_sort=0, claim_chunks=0, scoring=1), dict(process_sort=0, scoring=1),
               dict(l2_persist=1), dict(l2_persist=1, scoring=1, mode=1),
               dict(pipeline=1), dict(pipeline=1, along_steps=1, steps_per_claim=3),
-              dict(pipeline=1, mode=1, block_size=128)]
+              dict(pipeline=1, mode=1, block_size=128),
+              dict(local_stack=1), dict(local_stack=1, steps_per_claim=3, block_size=64),
+              dict(local_stack=1, tail_steps_per_claim=16, tail_threshold=1 << 40, scoring=1)]
     for kw in shapes:
         ctx = _ctx(gvmod, wl, per_event_counts=1, **kw)
         r = ctx.transport(per_event=True)

@@ -162,6 +162,9 @@ typedef struct {
                                  secondaries a block makes in a shared-memory stack and gives them to
                                  its idle lanes in the following rounds (the StackBuffer, Sec. 2.1.2)
                                  instead of leaving them to the next generation */
+  int pdl;                    /* 1 (default): successive step kernels of a graph use programmatic dependent
+                                 launch: a generation's blocks stage their tables while the previous
+                                 generation drains, and wait for it before reading its plan */
 } gv_config;
 
 /* A primary track; layout shared with the seeded input generator.  Its random

@@ -30,6 +30,7 @@ SPACE = {
     "along_steps": [2, 3, 4, 6],
     "scoring": [0, 1],
     "local_stack": [1, 0],
+    "pdl": [1, 0],
     "block_size": [128, 256],
     "blocks_per_sm": [2, 3, 4],
     "steps_per_claim": [1, 2, 3, 4],

@@ -667,7 +667,11 @@ __global__ void GV_STEP_BOUNDS
   __shared__ unsigned s_walive[SORT ? 16 : 1];
   Ctl *ctl = S->ctl;
   const int tid = threadIdx.x;
-  if (ctl->done) return;  // uniform: nothing planned for this generation
+  // Programmatic dependent launch (pdl): the next generation's blocks may
+  // start as soon as this one's finish, stage their tables, and wait for
+  // this grid (and its plan) to complete before reading the plan.
+  asm volatile("griddepcontrol.launch_dependents;");
+  if (ctl->done) return;  // a done flag seen before the wait is final: nothing planned
   // stage the cross-section tables and the geometry into shared memory
   {
     const uint4 *src = reinterpret_cast<const uint4 *>(S->view.xs);
@@ -693,14 +697,19 @@ __global__ void GV_STEP_BOUNDS
       sV.inv_node = idst;
       sV.smat = mdst;
       sV.smax = reinterpret_cast<const R *>(smem + S->smax_off);
-      for (int i = 0; i < 4; ++i) s_end[i] = ctl->chunk_end[i];
-      for (int r = 0; r <= kNClaim; ++r)
-        s_slice[r] = static_cast<unsigned>((static_cast<unsigned long long>(s_end[3]) * r) / kNClaim);
-      s_pb = ctl->prim_begin;
-      s_K = ctl->K;
-      s_ltop = 0;
     }
     if (tid < 16) bc.c[tid] = 0;
+  }
+  // the previous generation, and its plan, complete before the plan is read
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (ctl->done) return;  // uniform: nothing planned for this generation
+  if (tid == 0) {
+    for (int i = 0; i < 4; ++i) s_end[i] = ctl->chunk_end[i];
+    for (int r = 0; r <= kNClaim; ++r)
+      s_slice[r] = static_cast<unsigned>((static_cast<unsigned long long>(s_end[3]) * r) / kNClaim);
+    s_pb = ctl->prim_begin;
+    s_K = ctl->K;
+    s_ltop = 0;
   }
   __syncthreads();
   const View<R> &V = sV;
@@ -1395,6 +1404,7 @@ int validate_cfg(const gv_config &c) {
   if (c.scoring < 0 || c.scoring > 1) return GV_ERR_BAD_ARG;
   if (c.l2_persist < 0 || c.l2_persist > 1) return GV_ERR_BAD_ARG;
   if (c.local_stack < 0 || c.local_stack > 1) return GV_ERR_BAD_ARG;
+  if (c.pdl < 0 || c.pdl > 1) return GV_ERR_BAD_ARG;
   if (c.pipeline < 0 || c.pipeline > 1 || (c.pipeline == 1 && c.scoring != 0)) return GV_ERR_BAD_ARG;
   return GV_OK;
 }
@@ -1652,8 +1662,25 @@ template <typename R> int capture_graph(Ctx *c) {
     }
   } else {
     const StepFn<R> step = pick_step_kernel<R>(c->cfg, c->geo.field_T != 0.0);
-    for (int i = 0; i < c->cfg.generations_per_graph; ++i)
-      step<<<c->grid, c->cfg.block_size, c->smem_bytes, c->stream>>>(S, i & 1);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    for (int i = 0; i < c->cfg.generations_per_graph; ++i) {
+      cudaLaunchConfig_t lc = {};
+      lc.gridDim = dim3(c->grid);
+      lc.blockDim = dim3(c->cfg.block_size);
+      lc.dynamicSmemBytes = c->smem_bytes;
+      lc.stream = c->stream;
+      lc.attrs = attr;
+      lc.numAttrs = (c->cfg.pdl && i > 0) ? 1 : 0;  // overlap with the previous generation's tail
+      const int parity = i & 1;
+      if (cudaLaunchKernelEx(&lc, step, static_cast<const DevState<R> *>(S), parity) != cudaSuccess) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(c->stream, &junk);
+        if (junk) cudaGraphDestroy(junk);
+        return GV_ERR_CUDA;
+      }
+    }
   }
   cudaError_t e = cudaStreamEndCapture(c->stream, &g);
   if (e != cudaSuccess) return GV_ERR_CUDA;
@@ -1859,6 +1886,7 @@ int gv_default_config(gv_config *cfg) {
   cfg->l2_persist = 0;
   cfg->pipeline = 0;
   cfg->local_stack = 1;
+  cfg->pdl = 1;
   return GV_OK;
 }
 

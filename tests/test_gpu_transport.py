@@ -325,3 +325,27 @@ def test_largest_geometry_and_material_set(gvmod, oracle_mod):
     assert r32["status"] == 0
     layer_parity(wl, r32["edep"], ref["edep"])
     assert np.allclose(r32["cell"].sum((1, 2)), r32["edep"].reshape(400, 128, 8).sum((0, 2)), rtol=1e-9)
+
+
+# ---------------------------------------------------------------- concurrency
+def test_contexts_transport_concurrently(gvmod):
+    """Two contexts driven from two host threads at once (each with its own
+    work stream and buffers) give the results they give one at a time."""
+    import threading
+    wls = [W.pbps_electrons(200, 3000.0), W.with_msc(W.pblar_testem3(100, 3000.0))]
+    ctxs = [_ctx(gvmod, wl, per_event_counts=1) for wl in wls]
+    alone = [c.transport(per_event=True) for c in ctxs]
+    both = [None, None]
+
+    def run(i):
+        both[i] = ctxs[i].transport(per_event=True)
+
+    th = [threading.Thread(target=run, args=(i,)) for i in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for a, b in zip(alone, both):
+        assert b["status"] == 0
+        assert np.array_equal(a["counts"][:, :11], b["counts"][:, :11])
+        assert np.allclose(a["edep"], b["edep"], rtol=1e-9, atol=1e-9)

@@ -91,6 +91,7 @@ struct GeoConst {
   double hx, hy, pitch_x, pitch_y;
   double wx[2], wy[2];  // the x and y walls {-h, +h}
   float inv_pitch_x, inv_pitch_y;
+  float hx_lo, hy_lo;   // the half widths rounded down to FP32
   int walls_x, walls_y; // 0: unbounded in that direction
   int field_axis;       // uniform magnetic field along x, y or z
 };
@@ -357,6 +358,17 @@ __device__ R alias_sample(const View<R> &V, int m, R E, R ug, R ub, R ui, R *xi_
 // divided in R.  next = -1 when the track leaves the box.  The plane is
 // chosen before the subtraction, so a warp whose lanes move both ways still
 // issues one FP64 difference per axis.
+// An FP32 upper bound of |x| from the high word of the double (exponent
+// and top 20 significand bits, one unit up), in integer arithmetic: no FP64
+// instruction.  Inf where the exponent does not fit FP32.
+__device__ __forceinline__ float abs_upper_f(double x) {
+  const unsigned hi = static_cast<unsigned>(__double2hiint(x)) & 0x7fffffffu;
+  const int e = static_cast<int>(hi >> 20) - 1023 + 127;
+  if (e <= 0) return 1.17549435e-38f;  // |x| below the FP32 normal range
+  if (e >= 255) return __int_as_float(0x7f800000);
+  return __uint_as_float((static_cast<unsigned>(e) << 23) + (((hi & 0xfffffu) + 1u) << 3));
+}
+
 template <typename R>
 __device__ __forceinline__ R distance(const View<R> &V, double x, double y, double z, R u, R v, R w, int sub,
                                       int &next, int &plane) {
@@ -369,11 +381,16 @@ __device__ __forceinline__ R distance(const View<R> &V, double x, double y, doub
     nx = up ? sub + 1 : sub - 1;
     d = q_div(static_cast<R>(V.zb[pl] - z), w);
   }
-  if (V.geo.walls_x && u != R(0)) {
+  // A wall is at least h - |x| away along any direction: when that bound,
+  // from integer arithmetic, clears the plane distance with margin, the wall
+  // cannot be the nearest boundary and its FP64 difference is skipped (the
+  // result is the one the full test would give).
+  const float dz_f = static_cast<float>(d);
+  if (V.geo.walls_x && u != R(0) && !(V.geo.hx_lo - abs_upper_f(x) > 1.001f * dz_f + 1e-4f)) {
     const R dx = q_div(static_cast<R>(V.geo.wx[u > R(0) ? 1 : 0] - x), u);
     if (dx < d) { d = dx; nx = -1; pl = -2; }
   }
-  if (V.geo.walls_y && v != R(0)) {
+  if (V.geo.walls_y && v != R(0) && !(V.geo.hy_lo - abs_upper_f(y) > 1.001f * dz_f + 1e-4f)) {
     const R dy = q_div(static_cast<R>(V.geo.wy[v > R(0) ? 1 : 0] - y), v);
     if (dy < d) { d = dy; nx = -1; pl = -3; }
   }

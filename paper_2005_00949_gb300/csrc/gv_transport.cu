@@ -1529,6 +1529,13 @@ template <typename R> View<R> make_view(const Ctx *c) {
   v.geo.wx[1] = c->geo.half_x_cm;
   v.geo.wy[0] = -c->geo.half_y_cm;
   v.geo.wy[1] = c->geo.half_y_cm;
+  {  // the half widths rounded down to FP32
+    float fx = static_cast<float>(c->geo.half_x_cm), fy = static_cast<float>(c->geo.half_y_cm);
+    if (static_cast<double>(fx) > c->geo.half_x_cm) fx = std::nextafter(fx, 0.0f);
+    if (static_cast<double>(fy) > c->geo.half_y_cm) fy = std::nextafter(fy, 0.0f);
+    v.geo.hx_lo = fx;
+    v.geo.hy_lo = fy;
+  }
   v.geo.walls_x = c->geo.half_x_cm > 0.0;
   v.geo.walls_y = c->geo.half_y_cm > 0.0;
   v.geo.field_axis = c->geo.field_axis;

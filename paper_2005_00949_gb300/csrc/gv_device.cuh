@@ -420,10 +420,6 @@ __device__ R alias_sample(const View<R> &V, int m, R E, R ug, R ub, R ui, R *xi_
 }
 
 // ---------------------------------------------------------------- geometry
-// Distance to the boundary of sub-slab `sub`: FP64 coordinate differences,
-// divided in R.  next = -1 when the track leaves the box.  The plane is
-// chosen before the subtraction, so a warp whose lanes move both ways still
-// issues one FP64 difference per axis.
 // An FP32 upper bound of |x| from the high word of the double (exponent
 // and top 20 significand bits, one unit up), in integer arithmetic: no FP64
 // instruction.  Inf where the exponent does not fit FP32.  For a pair of
@@ -437,6 +433,10 @@ __device__ __forceinline__ float abs_upper_f(double x) {
   return __uint_as_float((static_cast<unsigned>(e) << 23) + (((hi & 0xfffffu) + 1u) << 3));
 }
 
+// Distance to the boundary of sub-slab `sub`: position differences, divided
+// in R.  next = -1 when the track leaves the box.  The plane is chosen
+// before the subtraction, so a warp whose lanes move both ways still issues
+// one difference per axis.
 template <typename R>
 __device__ __forceinline__ R distance(const View<R> &V, Pos<R> x, Pos<R> y, Pos<R> z, R u, R v, R w, int sub,
                                       int &next, int &plane) {

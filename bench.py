@@ -338,7 +338,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": "e-10GeV_PbPS50_2000: 2000 x 10 GeV e- on "
                                "50 x (2 mm Pb + 5 mm polystyrene), 40x40 cm, cuts 1 MeV",
-                   "events_per_gpu": wl.n_events, "precision": "mixed: FP32 physics, two-word FP32 positions, FP64 tallies",
+                   "events_per_gpu": wl.n_events, "precision": "mixed FP32 physics / FP64 positions",
                    "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"events x{world}"},
         "steps_per_s": steps_per_s,
         "track_steps_per_step": steps_tot / args.steps / 1.0,

@@ -53,7 +53,7 @@ extern "C" {
                                    accepted with the post-step cross sections */
 
 /* arithmetic of the stepping loop */
-#define GV_MIXED 0 /* FP32 physics, tables and energies; positions and boundaries as two FP32 words; FP64 tallies */
+#define GV_MIXED 0 /* FP32 physics, tables and energies; FP64 positions and boundaries */
 #define GV_FP64 1  /* FP64 everywhere */
 
 /* scheduling */

@@ -61,56 +61,9 @@ template <typename R> __device__ __forceinline__ R r_inf();
 template <> __device__ __forceinline__ float r_inf<float>() { return __int_as_float(0x7f800000); }
 template <> __device__ __forceinline__ double r_inf<double>() { return __longlong_as_double(0x7ff0000000000000ll); }
 
-// ---------------------------------------------------------------- positions
-// The FP64 kernels keep a coordinate in a double.  The mixed kernels keep it
-// as the unevaluated sum hi + lo of two FP32 words (|lo| <= ulp(hi)/2 after
-// every update: 48 significant bits, under 1e-13 cm at 20 cm) and advance it
-// with error-free FP32 additions, so that a step issues no FP64 instruction:
-// on GB300 the FP64 pipe, which also carries every FP32<->FP64 conversion,
-// runs at 1/64 of the FP32 rate.  Both take 8 bytes.
-struct alignas(8) F2 {
-  float hi, lo;
-};
-template <typename R> struct PosOf { using T = double; };
-template <> struct PosOf<float> { using T = F2; };
-template <typename R> using Pos = typename PosOf<R>::T;
-
-template <typename R> __host__ __device__ inline Pos<R> to_pos(double x);
-template <> __host__ __device__ inline double to_pos<double>(double x) { return x; }
-template <> __host__ __device__ inline F2 to_pos<float>(double x) {
-  const float h = static_cast<float>(x);
-  return F2{h, static_cast<float>(x - static_cast<double>(h))};
-}
-__device__ __forceinline__ double pos_f64(double p) { return p; }
-__device__ __forceinline__ double pos_f64(F2 p) { return static_cast<double>(p.hi) + static_cast<double>(p.lo); }
-
-// p += d.  The FP32 form: Knuth's two-sum of hi and d (exact), the error
-// folded into lo, then Dekker's fast two-sum to renormalise.
-__device__ __forceinline__ void pos_add(double &p, double d) { p += d; }
-__device__ __forceinline__ void pos_add(F2 &p, float d) {
-  const float s = p.hi + d;
-  const float bb = s - p.hi;
-  const float err = (p.hi - (s - bb)) + (d - bb);
-  const float l = p.lo + err;
-  const float h = s + l;
-  p.lo = l - (h - s);
-  p.hi = h;
-}
-// a - b in the kernel's precision (the FP32 form is exact in hi - hi
-// whenever a and b are within a factor 2 of each other)
-__device__ __forceinline__ double pos_sub(double a, double b) { return a - b; }
-__device__ __forceinline__ float pos_sub(F2 a, F2 b) { return (a.hi - b.hi) + (a.lo - b.lo); }
-__device__ __forceinline__ double pos_abs(double a) { return fabs(a); }
-__device__ __forceinline__ F2 pos_abs(F2 a) { return a.hi < 0.0f ? F2{-a.hi, -a.lo} : a; }
-// non-finite, tested on the exponent bits (no FP64 comparison)
-__device__ __forceinline__ bool pos_bad(double p) { return (__double2hiint(p) & 0x7ff00000) == 0x7ff00000; }
-__device__ __forceinline__ bool pos_bad(F2 p) { return (__float_as_uint(p.hi) & 0x7f800000u) == 0x7f800000u; }
-// the offset p + h from the low wall, in FP32 (cell indices)
-__device__ __forceinline__ float wall_offset(double p, double h, float) { return static_cast<float>(p + h); }
-__device__ __forceinline__ float wall_offset(F2 p, double, float hf) { return (p.hi + hf) + p.lo; }
-
-// exact float -> double from the bits, without the FP64 pipe (zeros and
-// normal numbers; subnormals and non-finite values take the conversion)
+// Exact float -> double from the bits, without the FP64 pipe (on GB300 it
+// also carries every conversion, at 1/64 of the FP32 rate).  Zeros and
+// normal numbers; subnormals and non-finite values take the instruction.
 __device__ __forceinline__ double f2d(float f) {
   const unsigned b = __float_as_uint(f);
   const unsigned e = (b >> 23) & 0xffu;
@@ -154,7 +107,6 @@ struct GeoConst {
   double wx[2], wy[2];  // the x and y walls {-h, +h}
   float inv_pitch_x, inv_pitch_y;
   float hx_lo, hy_lo;   // the half widths rounded down to FP32
-  float hx_f, hy_f;     // the half widths rounded to FP32
   int walls_x, walls_y; // 0: unbounded in that direction
   int field_axis;       // uniform magnetic field along x, y or z
 };
@@ -179,8 +131,7 @@ template <typename R> struct RConst {
 template <typename R> struct View {
   const V4<R> *xs;           // [(mat*3 + type)*kGridN + node], smem or global
   const float *inv_node;     // 1/E_i of the grid nodes (FP32 lookups)
-  const Pos<R> *zb;          // nsub+1 planes, smem or global
-  const double *zb64;        // the same planes in FP64 (locating primaries)
+  const double *zb;          // nsub+1 planes
   const unsigned char *smat; // material of each sub-slab
   const AliasBin<R> *bins;   // all models, [off + ie*kNB + j]
   const R *smax;             // integral approach bound [(mat*2 + type-1)*kGridN + node], smem or global
@@ -189,8 +140,6 @@ template <typename R> struct View {
   GeoConst geo;
   CutConst cut;
   RConst<R> rc;
-  Pos<R> wall_x[2], wall_y[2];  // the walls {-h, +h} as positions
-  Pos<R> half_x, half_y;
 };
 
 // ---------------------------------------------------------------- RNG
@@ -422,9 +371,7 @@ __device__ R alias_sample(const View<R> &V, int m, R E, R ug, R ub, R ui, R *xi_
 // ---------------------------------------------------------------- geometry
 // An FP32 upper bound of |x| from the high word of the double (exponent
 // and top 20 significand bits, one unit up), in integer arithmetic: no FP64
-// instruction.  Inf where the exponent does not fit FP32.  For a pair of
-// FP32 words, |hi| (1 + 2^-22) >= |hi| + |lo|.
-__device__ __forceinline__ float abs_upper_f(F2 x) { return fabsf(x.hi) * 1.00000024f; }
+// instruction.  Inf where the exponent does not fit FP32.
 __device__ __forceinline__ float abs_upper_f(double x) {
   const unsigned hi = static_cast<unsigned>(__double2hiint(x)) & 0x7fffffffu;
   const int e = static_cast<int>(hi >> 20) - 1023 + 127;
@@ -433,12 +380,12 @@ __device__ __forceinline__ float abs_upper_f(double x) {
   return __uint_as_float((static_cast<unsigned>(e) << 23) + (((hi & 0xfffffu) + 1u) << 3));
 }
 
-// Distance to the boundary of sub-slab `sub`: position differences, divided
-// in R.  next = -1 when the track leaves the box.  The plane is chosen
-// before the subtraction, so a warp whose lanes move both ways still issues
-// one difference per axis.
+// Distance to the boundary of sub-slab `sub`: FP64 coordinate differences,
+// divided in R.  next = -1 when the track leaves the box.  The plane is
+// chosen before the subtraction, so a warp whose lanes move both ways still
+// issues one FP64 difference per axis.
 template <typename R>
-__device__ __forceinline__ R distance(const View<R> &V, Pos<R> x, Pos<R> y, Pos<R> z, R u, R v, R w, int sub,
+__device__ __forceinline__ R distance(const View<R> &V, double x, double y, double z, R u, R v, R w, int sub,
                                       int &next, int &plane) {
   GV_CHECK(V.status, sub >= 0 && sub < V.geo.nsub);
   R d = r_inf<R>();
@@ -447,7 +394,7 @@ __device__ __forceinline__ R distance(const View<R> &V, Pos<R> x, Pos<R> y, Pos<
     const int up = w > R(0) ? 1 : 0;
     pl = sub + up;
     nx = up ? sub + 1 : sub - 1;
-    d = q_div(static_cast<R>(pos_sub(V.zb[pl], z)), w);
+    d = q_div(static_cast<R>(V.zb[pl] - z), w);
   }
   // A wall is at least h - |x| away along any direction: when that bound,
   // from integer arithmetic, clears the plane distance with margin, the wall
@@ -455,11 +402,11 @@ __device__ __forceinline__ R distance(const View<R> &V, Pos<R> x, Pos<R> y, Pos<
   // result is the one the full test would give).
   const float dz_f = static_cast<float>(d);
   if (V.geo.walls_x && u != R(0) && !(V.geo.hx_lo - abs_upper_f(x) > 1.001f * dz_f + 1e-4f)) {
-    const R dx = q_div(static_cast<R>(pos_sub(V.wall_x[u > R(0) ? 1 : 0], x)), u);
+    const R dx = q_div(static_cast<R>(V.geo.wx[u > R(0) ? 1 : 0] - x), u);
     if (dx < d) { d = dx; nx = -1; pl = -2; }
   }
   if (V.geo.walls_y && v != R(0) && !(V.geo.hy_lo - abs_upper_f(y) > 1.001f * dz_f + 1e-4f)) {
-    const R dy = q_div(static_cast<R>(pos_sub(V.wall_y[v > R(0) ? 1 : 0], y)), v);
+    const R dy = q_div(static_cast<R>(V.geo.wy[v > R(0) ? 1 : 0] - y), v);
     if (dy < d) { d = dy; nx = -1; pl = -3; }
   }
   if (d < R(0)) d = R(0);
@@ -601,8 +548,8 @@ __device__ __forceinline__ void helix(const View<R> &V, int type, R E, R s, cons
 // shortened to 0.99 of the safety (distance to the nearest boundary of
 // sub-slab `sub`, from FP64 differences) when longer.
 template <typename R>
-__device__ __forceinline__ void msc_step(const View<R> &V, int sub, R E_pre, R E_post, R s, R d[3], Pos<R> &x,
-                                         Pos<R> &y, Pos<R> &z, const R u[4]) {
+__device__ __forceinline__ void msc_step(const View<R> &V, int sub, R E_pre, R E_post, R s, R d[3], double &x,
+                                         double &y, double &z, const R u[4]) {
   const R ME = static_cast<R>(kME);
   const R T = R(0.5) * (E_pre + E_post);
   const R pc = m_sqrt(T * (T + R(2) * ME));
@@ -632,22 +579,22 @@ __device__ __forceinline__ void msc_step(const View<R> &V, int sub, R E_pre, R E
   }
   // offset, limited by the safety of the pre-move end point
   const R len = m_sqrt(ox * ox + oy * oy);
-  R sf = pos_sub(z, V.zb[sub]);
-  const R sz2 = pos_sub(V.zb[sub + 1], z);
+  double sf = z - V.zb[sub];
+  const double sz2 = V.zb[sub + 1] - z;
   sf = sz2 < sf ? sz2 : sf;
   if (V.geo.walls_x) {
-    const R sx = pos_sub(V.half_x, pos_abs(x));
+    const double sx = V.geo.hx - fabs(x);
     sf = sx < sf ? sx : sf;
   }
   if (V.geo.walls_y) {
-    const R sy = pos_sub(V.half_y, pos_abs(y));
+    const double sy = V.geo.hy - fabs(y);
     sf = sy < sf ? sy : sf;
   }
-  const R safe = sf > R(0) ? sf : R(0);
+  const R safe = sf > 0.0 ? static_cast<R>(sf) : R(0);
   const R scale = (len > R(0.99) * safe) ? (len > R(0) ? R(0.99) * safe / len : R(0)) : R(1);
-  pos_add(x, scale * (ox * e1[0] + oy * e2[0]));
-  pos_add(y, scale * (ox * e1[1] + oy * e2[1]));
-  pos_add(z, scale * (ox * e1[2] + oy * e2[2]));
+  x += f2d(scale * (ox * e1[0] + oy * e2[0]));
+  y += f2d(scale * (ox * e1[1] + oy * e2[1]));
+  z += f2d(scale * (ox * e1[2] + oy * e2[2]));
   // direction
   R th = m_sqrt(tx * tx + ty * ty);
   if (!(th > R(0))) return;

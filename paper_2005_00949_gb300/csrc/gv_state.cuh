@@ -9,7 +9,7 @@ namespace gv {
 
 // Structure-of-arrays queue of one particle type.
 template <typename R> struct Queue {
-  Pos<R> *x, *y, *z;
+  double *x, *y, *z;
   R *u, *v, *w, *E, *nlam;
   unsigned long long *id;
   unsigned *ev, *step;
@@ -23,7 +23,7 @@ constexpr int kFlagPrimary = 1;
 constexpr int kFlagInteracted = 2;
 
 template <typename R> constexpr size_t track_bytes() {
-  return 3 * sizeof(Pos<R>) + 5 * sizeof(R) + sizeof(unsigned long long) + 3 * sizeof(unsigned);
+  return 3 * sizeof(double) + 5 * sizeof(R) + sizeof(unsigned long long) + 3 * sizeof(unsigned);
 }
 
 // Claim counters of the work slices, one per 128-byte line.
@@ -36,7 +36,7 @@ struct alignas(128) ClaimSlot {
 // a track that is due a discrete interaction to the interaction kernel
 // (one 16-byte-aligned record per request).
 template <typename R> struct alignas(16) GReq {
-  Pos<R> x, y, z;
+  double x, y, z;
   unsigned long long id;
   R E, d0, d1, d2;
   R u[6];        // u2..u7 of the step

@@ -50,8 +50,8 @@ template <typename R> __device__ __forceinline__ void kahan_add(R &sum, R &comp,
 }
 
 template <typename R>
-__device__ __forceinline__ void deposit(const View<R> &V, const DevState<R> *S, unsigned ev, int sub, Pos<R> px,
-                                        Pos<R> py, R dE, Pending<R> *pd = nullptr) {
+__device__ __forceinline__ void deposit(const View<R> &V, const DevState<R> *S, unsigned ev, int sub, double px,
+                                        double py, R dE, Pending<R> *pd = nullptr) {
   if (!(dE != R(0)) || sub < 0) return;
   GV_CHECK(&S->ctl->status, ev < S->n_events && sub < V.geo.nsub);
   const unsigned long long key = static_cast<unsigned long long>(ev) * V.geo.nsub + sub;
@@ -73,8 +73,8 @@ __device__ __forceinline__ void deposit(const View<R> &V, const DevState<R> *S, 
     const int layer = sub / g.nsub_layer;
     // the offset from the wall in FP64, the cell index in FP32 (a cell
     // edge moves by ~1e-7 of the box width; no FP64 division)
-    int ix = __float2int_rd(wall_offset(px, g.hx, g.hx_f) * g.inv_pitch_x);
-    int iy = __float2int_rd(wall_offset(py, g.hy, g.hy_f) * g.inv_pitch_y);
+    int ix = __float2int_rd(static_cast<float>(px + g.hx) * g.inv_pitch_x);
+    int iy = __float2int_rd(static_cast<float>(py + g.hy) * g.inv_pitch_y);
     ix = ix < 0 ? 0 : (ix >= g.nx ? g.nx - 1 : ix);
     iy = iy < 0 ? 0 : (iy >= g.ny ? g.ny - 1 : iy);
     atomicAdd(&S->cell[(static_cast<size_t>(layer) * g.nx + ix) * g.ny + iy], f2d(dE));
@@ -107,7 +107,7 @@ __device__ __forceinline__ void count(const DevState<R> *S, BlockCnt *bc, unsign
 }
 
 template <typename R> struct Trk {
-  Pos<R> x, y, z;
+  double x, y, z;
   R u, v, w, E, nlam;
   unsigned long long id;
   unsigned ev, step;
@@ -215,41 +215,43 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
     if (t.type == 2) count(S, bc, t.ev, GV_C_EP_ESC);
     return 0;
   }
-  // Propagation: positions advanced by displacements s d formed in R (s and
-  // d are R already; in FP64 mode this is one fused multiply-add)
-  Pos<R> mx = t.x, my = t.y;  // step midpoint: only cell scoring reads it
+  // Propagation: FP64 positions, advanced by displacements s d formed in R
+  // (s and d are R already; an FP32 displacement is widened exactly on the
+  // integer ALU, leaving the FP64 pipe one addition per coordinate; in FP64
+  // mode this is one fused multiply-add)
+  double mx = 0.0, my = 0.0;  // step midpoint: only cell scoring reads it
   if (FIELD && charged && V.rc.field_k != R(0)) {  // the helix of the pre-step momentum
     const R d0[3] = {t.u, t.v, t.w};
     R dp[3], nd[3];
     if (S->cell) {
       helix(V, t.type, t.E, R(0.5) * s, d0, dp, nd);
-      pos_add(mx, dp[0]);
-      pos_add(my, dp[1]);
+      mx = t.x + f2d(dp[0]);
+      my = t.y + f2d(dp[1]);
     }
     helix(V, t.type, t.E, s, d0, dp, nd);
-    pos_add(t.x, dp[0]);
-    pos_add(t.y, dp[1]);
-    pos_add(t.z, dp[2]);
+    t.x += f2d(dp[0]);
+    t.y += f2d(dp[1]);
+    t.z += f2d(dp[2]);
     if (lim == 0) {  // the crossed plane, chosen with the pre-step direction
       if (plane >= 0) t.z = V.zb[plane];
-      else if (plane == -2) t.x = V.wall_x[t.u > R(0) ? 1 : 0];
-      else if (plane == -3) t.y = V.wall_y[t.v > R(0) ? 1 : 0];
+      else if (plane == -2) t.x = V.geo.wx[t.u > R(0) ? 1 : 0];
+      else if (plane == -3) t.y = V.geo.wy[t.v > R(0) ? 1 : 0];
     }
     t.u = nd[0];
     t.v = nd[1];
     t.w = nd[2];
   } else {
     if (S->cell) {
-      pos_add(mx, R(0.5) * s * t.u);
-      pos_add(my, R(0.5) * s * t.v);
+      mx = t.x + f2d(R(0.5) * s * t.u);
+      my = t.y + f2d(R(0.5) * s * t.v);
     }
-    pos_add(t.x, s * t.u);
-    pos_add(t.y, s * t.v);
-    pos_add(t.z, s * t.w);
+    t.x += f2d(s * t.u);
+    t.y += f2d(s * t.v);
+    t.z += f2d(s * t.w);
     if (lim == 0) {
       if (plane >= 0) t.z = V.zb[plane];
-      else if (plane == -2) t.x = V.wall_x[t.u > R(0) ? 1 : 0];
-      else if (plane == -3) t.y = V.wall_y[t.v > R(0) ? 1 : 0];
+      else if (plane == -2) t.x = V.geo.wx[t.u > R(0) ? 1 : 0];
+      else if (plane == -3) t.y = V.geo.wy[t.v > R(0) ? 1 : 0];
     }
   }
   if (Smax > R(0)) t.nlam = (lim == 1) ? R(0) : t.nlam - s * Smax;
@@ -334,7 +336,7 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
 template <typename R>
 __device__ __forceinline__ int final_state(const View<R> &V, const DevState<R> *S, BlockCnt *bc, int type, int proc,
                                            R &E, R d[3], const R *u, Kids<R> &kids, unsigned ev, int sub,
-                                           Pos<R> x, Pos<R> y, unsigned long long id, uint32_t kk,
+                                           double x, double y, unsigned long long id, uint32_t kk,
                                            Pending<R> *pd = nullptr) {
   R local;
   int np = 0, na = 0;
@@ -367,7 +369,7 @@ __device__ __forceinline__ unsigned warp_reserve(unsigned *counter, unsigned c, 
 }
 
 template <typename R>
-__device__ __forceinline__ void store(const Queue<R> &q, unsigned slot, Pos<R> x, Pos<R> y, Pos<R> z, R u, R v, R w,
+__device__ __forceinline__ void store(const Queue<R> &q, unsigned slot, double x, double y, double z, R u, R v, R w,
                                       R E, R nlam, unsigned long long id, unsigned ev, unsigned step, int sf) {
   q.x[slot] = x;
   q.y[slot] = y;
@@ -385,15 +387,15 @@ __device__ __forceinline__ void store(const Queue<R> &q, unsigned slot, Pos<R> x
 
 // The parent of a step's secondaries: where they start and whose lineage
 // names them.
-template <typename R> struct Parent {
-  Pos<R> x, y, z;
+struct Parent {
+  double x, y, z;
   unsigned long long id;
   unsigned ev;
   int sub;
 };
 
-template <typename R> __device__ __forceinline__ Parent<R> parent_of(const Trk<R> &t) {
-  Parent<R> p;
+template <typename R> __device__ __forceinline__ Parent parent_of(const Trk<R> &t) {
+  Parent p;
   p.x = t.x; p.y = t.y; p.z = t.z;
   p.id = t.id;
   p.ev = t.ev;
@@ -405,7 +407,7 @@ template <typename R> __device__ __forceinline__ Parent<R> parent_of(const Trk<R
 // Sec. 2.1.2 for one block): its lanes take it up in a later round of the
 // same claim instead of leaving it to the next generation.
 template <typename R> struct LKid {
-  Pos<R> x, y, z;
+  double x, y, z;
   unsigned long long id;
   R u, v, w, E;
   unsigned ev;
@@ -425,7 +427,7 @@ template <typename R> struct LocalStack {
 // with a local stack, to the block's stack while it has room.  Called by all
 // 32 lanes of a converged warp (lanes without secondaries pass kids.n == 0).
 template <typename R>
-__device__ void push_kids(const DevState<R> *S, int out, const Parent<R> &t, const Kids<R> &kids, uint32_t kk,
+__device__ void push_kids(const DevState<R> *S, int out, const Parent &t, const Kids<R> &kids, uint32_t kk,
                           BlockCnt *bc, const LocalStack<R> *ls = nullptr) {
   const unsigned any = __ballot_sync(0xffffffffu, kids.n > 0);
   if (!any) return;
@@ -499,7 +501,7 @@ template <typename R> __device__ __forceinline__ void track_ended(const DevState
 
 // An interaction request staged in shared memory by the in-block basketizer.
 template <typename R> struct IReq {
-  Pos<R> x, y, z;
+  double x, y, z;
   unsigned long long id;
   R E, d0, d1, d2;
   R u[6];      // u2..u7 of the step
@@ -677,8 +679,8 @@ __global__ void GV_STEP_BOUNDS
     const uint4 *src = reinterpret_cast<const uint4 *>(S->view.xs);
     uint4 *dst = reinterpret_cast<uint4 *>(smem);
     for (unsigned i = tid; i < S->xs_bytes / 16; i += blockDim.x) dst[i] = src[i];
-    const Pos<R> *zsrc = S->view.zb;
-    Pos<R> *zdst = reinterpret_cast<Pos<R> *>(smem + S->xs_bytes);
+    const double *zsrc = S->view.zb;
+    double *zdst = reinterpret_cast<double *>(smem + S->xs_bytes);
     const int nz = S->view.geo.nsub + 1;
     for (int i = tid; i < nz; i += blockDim.x) zdst[i] = zsrc[i];
     float *idst = reinterpret_cast<float *>(smem + S->xs_bytes + S->zb_bytes);
@@ -805,14 +807,14 @@ __global__ void GV_STEP_BOUNDS
       }
       t.type = p.type;
       t.E = static_cast<R>(p.E_MeV);
-      t.x = to_pos<R>(p.x); t.y = to_pos<R>(p.y); t.z = to_pos<R>(p.z);
+      t.x = p.x; t.y = p.y; t.z = p.z;
       t.u = static_cast<R>(p.u); t.v = static_cast<R>(p.v); t.w = static_cast<R>(p.w);
       t.nlam = R(-1);
       t.id = p.id;
       t.ev = p.event;
       t.step = 0;
       t.flags = kFlagPrimary;
-      t.sub = locate(V.zb64, V.geo.nsub, p.z, p.w);
+      t.sub = locate(V.zb, V.geo.nsub, p.z, p.w);
       count(S, &bc, t.ev, GV_C_TRK_G + t.type);
       if (t.sub < 0) {
         atomicAdd(&S->escape[t.ev], p.E_MeV);
@@ -863,7 +865,7 @@ __global__ void GV_STEP_BOUNDS
         alive = step_track<R, FIELD>(V, S, t, kids, kstep, &bc, proc, u, lim, pd) != 0;
         // NaN energy, or a non-finite z (tested on its exponent bits: an FP64
         // comparison would take the FP64 pipe)
-        if (!(t.E == t.E) || pos_bad(t.z)) {
+        if (!(t.E == t.E) || (__double2hiint(t.z) & 0x7ff00000) == 0x7ff00000) {
           set_status(ctl, GV_ERR_NUMERIC);
           alive = false;
           proc = -1;
@@ -959,7 +961,7 @@ __global__ void GV_STEP_BOUNDS
         __syncthreads();
         Kids<R> kb;
         kb.n = 0;
-        Parent<R> par;
+        Parent par;
         uint32_t pk = 0;
         if (static_cast<unsigned>(tid) < nreq) {
           IReq<R> &q = req[tid];
@@ -1080,8 +1082,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_ALONG_MIN_BLOCKS : 2)
     const uint4 *src = reinterpret_cast<const uint4 *>(S->view.xs);
     uint4 *dst = reinterpret_cast<uint4 *>(smem);
     for (unsigned i = tid; i < S->xs_bytes / 16; i += blockDim.x) dst[i] = src[i];
-    const Pos<R> *zsrc = S->view.zb;
-    Pos<R> *zdst = reinterpret_cast<Pos<R> *>(smem + S->xs_bytes);
+    const double *zsrc = S->view.zb;
+    double *zdst = reinterpret_cast<double *>(smem + S->xs_bytes);
     const int nz = S->view.geo.nsub + 1;
     for (int i = tid; i < nz; i += blockDim.x) zdst[i] = zsrc[i];
     float *idst = reinterpret_cast<float *>(smem + S->xs_bytes + S->zb_bytes);
@@ -1150,14 +1152,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_ALONG_MIN_BLOCKS : 2)
       }
       t.type = p.type;
       t.E = static_cast<R>(p.E_MeV);
-      t.x = to_pos<R>(p.x); t.y = to_pos<R>(p.y); t.z = to_pos<R>(p.z);
+      t.x = p.x; t.y = p.y; t.z = p.z;
       t.u = static_cast<R>(p.u); t.v = static_cast<R>(p.v); t.w = static_cast<R>(p.w);
       t.nlam = R(-1);
       t.id = p.id;
       t.ev = p.event;
       t.step = 0;
       t.flags = kFlagPrimary;
-      t.sub = locate(V.zb64, V.geo.nsub, p.z, p.w);
+      t.sub = locate(V.zb, V.geo.nsub, p.z, p.w);
       count(S, &bc, t.ev, GV_C_TRK_G + t.type);
       if (t.sub < 0) {
         atomicAdd(&S->escape[t.ev], p.E_MeV);
@@ -1181,7 +1183,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_ALONG_MIN_BLOCKS : 2)
         ++n_iter;
         const uint32_t before = t.step;
         alive = step_track<R, true>(V, S, t, kids, kstep, &bc, proc, u, lim, static_cast<Pending<R> *>(nullptr)) != 0;
-        if (!(t.E == t.E) || pos_bad(t.z)) {
+        if (!(t.E == t.E) || (__double2hiint(t.z) & 0x7ff00000) == 0x7ff00000) {
           set_status(ctl, GV_ERR_NUMERIC);
           alive = false;
           proc = -1;
@@ -1258,7 +1260,7 @@ __global__ void __launch_bounds__(256) interact_kernel(const DevState<R> *__rest
     Trk<R> t;
     Kids<R> kids;
     kids.n = 0;
-    Parent<R> par;
+    Parent par;
     uint32_t kk = 0;
     bool alive = false;
     if (has) {
@@ -1282,7 +1284,7 @@ __global__ void __launch_bounds__(256) interact_kernel(const DevState<R> *__rest
       alive = r != 0;
       par = parent_of(t);
     } else {
-      par.x = par.y = par.z = to_pos<R>(0.0);
+      par.x = par.y = par.z = 0.0;
       par.id = 0;
       par.ev = 0;
       par.sub = 0;
@@ -1328,7 +1330,6 @@ struct Ctx {
   void *d_xs = nullptr, *d_bins = nullptr, *d_smax = nullptr;
   float *d_inv_node = nullptr;
   double *d_zb = nullptr;
-  F2 *d_zb2 = nullptr;  // the planes as pairs of FP32 words (mixed kernels)
   unsigned char *d_smat = nullptr;
   void *d_queues = nullptr;
   Ctl *d_ctl = nullptr;
@@ -1419,9 +1420,9 @@ template <typename R> Queue<R> carve(unsigned char *&p, long long cap) {
     p += (n + 255) / 256 * 256;
     return r;
   };
-  q.x = reinterpret_cast<Pos<R> *>(take(cap * sizeof(Pos<R>)));
-  q.y = reinterpret_cast<Pos<R> *>(take(cap * sizeof(Pos<R>)));
-  q.z = reinterpret_cast<Pos<R> *>(take(cap * sizeof(Pos<R>)));
+  q.x = reinterpret_cast<double *>(take(cap * sizeof(double)));
+  q.y = reinterpret_cast<double *>(take(cap * sizeof(double)));
+  q.z = reinterpret_cast<double *>(take(cap * sizeof(double)));
   q.u = reinterpret_cast<R *>(take(cap * sizeof(R)));
   q.v = reinterpret_cast<R *>(take(cap * sizeof(R)));
   q.w = reinterpret_cast<R *>(take(cap * sizeof(R)));
@@ -1509,21 +1510,11 @@ int setup_l2_window(Ctx *c) {
   return GV_OK;
 }
 
-inline const double *planes_of(const Ctx *c, double) { return c->d_zb; }
-inline const F2 *planes_of(const Ctx *c, float) { return c->d_zb2; }
-
 template <typename R> View<R> make_view(const Ctx *c) {
   View<R> v;
   v.xs = reinterpret_cast<const V4<R> *>(c->d_xs);
   v.inv_node = c->d_inv_node;
-  v.zb = planes_of(c, R(0));
-  v.zb64 = c->d_zb;
-  v.wall_x[0] = to_pos<R>(-c->geo.half_x_cm);
-  v.wall_x[1] = to_pos<R>(c->geo.half_x_cm);
-  v.wall_y[0] = to_pos<R>(-c->geo.half_y_cm);
-  v.wall_y[1] = to_pos<R>(c->geo.half_y_cm);
-  v.half_x = to_pos<R>(c->geo.half_x_cm);
-  v.half_y = to_pos<R>(c->geo.half_y_cm);
+  v.zb = c->d_zb;
   v.smat = c->d_smat;
   v.bins = reinterpret_cast<const AliasBin<R> *>(c->d_bins);
   v.smax = reinterpret_cast<const R *>(c->d_smax);
@@ -1546,8 +1537,6 @@ template <typename R> View<R> make_view(const Ctx *c) {
     if (static_cast<double>(fy) > c->geo.half_y_cm) fy = std::nextafter(fy, 0.0f);
     v.geo.hx_lo = fx;
     v.geo.hy_lo = fy;
-    v.geo.hx_f = static_cast<float>(c->geo.half_x_cm);
-    v.geo.hy_f = static_cast<float>(c->geo.half_y_cm);
   }
   v.geo.walls_x = c->geo.half_x_cm > 0.0;
   v.geo.walls_y = c->geo.half_y_cm > 0.0;
@@ -1944,11 +1933,7 @@ int gv_setup(void **ctx_out, const gv_material *mats, int n_mats, const gv_layer
     delete x;
     return GV_ERR_CUDA;
   }
-  std::vector<F2> zb2(x->nsub + 1);
-  for (int k = 0; k <= x->nsub; ++k) zb2[k] = to_pos<float>(x->zb[k]);
   if (cudaMalloc(&x->d_zb, sizeof(double) * (x->nsub + 1)) != cudaSuccess ||
-      cudaMalloc(&x->d_zb2, sizeof(F2) * (x->nsub + 1)) != cudaSuccess ||
-      cudaMemcpy(x->d_zb2, zb2.data(), sizeof(F2) * (x->nsub + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMalloc(&x->d_smat, x->nsub) != cudaSuccess ||
       cudaMemcpy(x->d_zb, x->zb.data(), sizeof(double) * (x->nsub + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(x->d_smat, x->smat.data(), x->nsub, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -2021,7 +2006,6 @@ void gv_destroy(void *ctx) {
   cudaFree(c->d_bins);
   cudaFree(c->d_smax);
   cudaFree(c->d_zb);
-  cudaFree(c->d_zb2);
   cudaFree(c->d_smat);
   cudaFree(c->d_queues);
   cudaFree(c->d_ctl);
@@ -2133,9 +2117,9 @@ Queue<float> carve_static(unsigned char *&p) {
     return r;
   };
   const size_t C = static_cast<size_t>(kStaticCap);
-  q.x = reinterpret_cast<F2 *>(take(C * sizeof(F2)));
-  q.y = reinterpret_cast<F2 *>(take(C * sizeof(F2)));
-  q.z = reinterpret_cast<F2 *>(take(C * sizeof(F2)));
+  q.x = reinterpret_cast<double *>(take(C * 8));
+  q.y = reinterpret_cast<double *>(take(C * 8));
+  q.z = reinterpret_cast<double *>(take(C * 8));
   q.u = reinterpret_cast<float *>(take(C * 4));
   q.v = reinterpret_cast<float *>(take(C * 4));
   q.w = reinterpret_cast<float *>(take(C * 4));

@@ -102,7 +102,7 @@ __global__ void k_distance(View<R> V, const double *pos, const double *dir, cons
     plane[i] = -1;
     return;
   }
-  const R d = distance(V, to_pos<R>(pos[3 * i]), to_pos<R>(pos[3 * i + 1]), to_pos<R>(pos[3 * i + 2]), static_cast<R>(dir[3 * i]),
+  const R d = distance(V, pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], static_cast<R>(dir[3 * i]),
                        static_cast<R>(dir[3 * i + 1]), static_cast<R>(dir[3 * i + 2]), sub[i], nx, pl);
   dist[i] = d;
   next[i] = nx;
@@ -122,14 +122,14 @@ __global__ void k_msc(View<R> V, const int *sub, const double *Ea, const double 
   R d[3] = {static_cast<R>(dir[3 * i]), static_cast<R>(dir[3 * i + 1]), static_cast<R>(dir[3 * i + 2])};
   const R uu[4] = {static_cast<R>(u[4 * i]), static_cast<R>(u[4 * i + 1]), static_cast<R>(u[4 * i + 2]),
                    static_cast<R>(u[4 * i + 3])};
-  Pos<R> x = to_pos<R>(pos[3 * i]), y = to_pos<R>(pos[3 * i + 1]), z = to_pos<R>(pos[3 * i + 2]);
+  double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
   msc_step(V, sub[i], static_cast<R>(Ea[i]), static_cast<R>(Eb[i]), static_cast<R>(sv[i]), d, x, y, z, uu);
   od[3 * i] = d[0];
   od[3 * i + 1] = d[1];
   od[3 * i + 2] = d[2];
-  op[3 * i] = pos_f64(x);
-  op[3 * i + 1] = pos_f64(y);
-  op[3 * i + 2] = pos_f64(z);
+  op[3 * i] = x;
+  op[3 * i + 1] = y;
+  op[3 * i + 2] = z;
 }
 
 template <typename R>

@@ -3,7 +3,7 @@
 FP64 mode: the GPU and the oracle draw the same Philox numbers for the same
 track step, so their histories coincide event by event unless rounding
 flips a branch; integer counts and deposits are compared per event.
-Mixed mode (FP32 physics, two-word FP32 positions): per-layer mean deposits must agree
+Mixed mode (FP32 physics, FP64 positions): per-layer mean deposits must agree
 within 3 combined standard errors on every layer, and within 0.5% on layers
 holding >= 1% of the deposit wherever the statistics resolve 0.5% at 3 sigma.
 """

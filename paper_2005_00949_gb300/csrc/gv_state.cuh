@@ -57,6 +57,7 @@ struct Ctl {
   unsigned claim;            // chunk claim counter
   unsigned blocks_done;
   int K;                     // steps per claimed track this generation
+  unsigned chunk_B;          // tracks per block claim this generation
   int status;
   int done;
   int pad;
@@ -102,6 +103,7 @@ template <typename R> struct DevState {
   unsigned smax_off, smax_bytes; // the integral approach's bound, staged into shared memory
   unsigned smem_lk_off;          // the block's secondary stack (local_stack)
   int local_stack;
+  int grid, adaptive_chunk;  // blocks of the step kernel; spread small populations over all of them
 };
 
 }  // namespace gv

@@ -579,7 +579,18 @@ template <typename R> __device__ void plan_next(const DevState<R> *S, int pn) {
   c->prim_begin = c->prim_next;
   c->prim_count = inj;
   c->prim_next += inj;
-  const unsigned B = static_cast<unsigned>(S->chunk);
+  unsigned B = static_cast<unsigned>(S->chunk);
+  // With fewer live tracks than the grid has lanes (the first generations of
+  // a shower and its tail), a block claims fewer tracks (a multiple of 32)
+  // so that every block gets some: each block's rounds are then short, with
+  // fewer warps to wait for at its barriers and its idle lanes left to the
+  // secondaries of its block stack.
+  if (S->adaptive_chunk) {
+    const unsigned long long tot = live + inj;
+    const unsigned long long per = (tot + S->grid - 1) / S->grid;
+    if (per < B) B = per <= 32 ? 32u : static_cast<unsigned>((per + 31) / 32 * 32);
+  }
+  c->chunk_B = B;
   c->chunk_end[0] = (n0 + B - 1) / B;
   c->chunk_end[1] = c->chunk_end[0] + (n1 + B - 1) / B;
   c->chunk_end[2] = c->chunk_end[1] + (n2 + B - 1) / B;
@@ -664,6 +675,7 @@ __global__ void GV_STEP_BOUNDS
   __shared__ unsigned s_chunk, s_end[4], s_pb;
   __shared__ unsigned s_slice[kNClaim + 1];
   __shared__ int s_K, s_last;
+  __shared__ unsigned s_B;
   __shared__ int s_ltop;  // the block's secondary stack (local_stack)
   __shared__ unsigned s_wcnt[SORT ? kNKey : 1][SORT ? 16 : 1];
   __shared__ unsigned s_walive[SORT ? 16 : 1];
@@ -711,6 +723,7 @@ __global__ void GV_STEP_BOUNDS
       s_slice[r] = static_cast<unsigned>((static_cast<unsigned long long>(s_end[3]) * r) / kNClaim);
     s_pb = ctl->prim_begin;
     s_K = ctl->K;
+    s_B = ctl->chunk_B;
     s_ltop = 0;
   }
   __syncthreads();
@@ -775,8 +788,9 @@ __global__ void GV_STEP_BOUNDS
     while (chunk >= s_end[qsel]) ++qsel;
     {
       const bool per_block = SORT || S->claim_chunks == 0;
-      const unsigned csize = per_block ? blockDim.x : 32u;
+      const unsigned csize = per_block ? s_B : 32u;
       idx = (chunk - (qsel ? s_end[qsel - 1] : 0u)) * csize + (per_block ? tid : (tid & 31));
+      if (per_block && static_cast<unsigned>(tid) >= csize) idx = 0xffffffffu;
     }
     Trk<R> t;
     bool alive = false;
@@ -1634,6 +1648,8 @@ template <typename R> DevState<R> make_state(Ctx *c) {
   s.view.status = &c->d_ctl->status;  // device address; checks of the checking build
   s.block_size = c->cfg.block_size;
   s.chunk = (c->cfg.pipeline || c->cfg.process_sort || c->cfg.claim_chunks == 0) ? c->cfg.block_size : 32;
+  s.grid = c->grid;
+  s.adaptive_chunk = (c->cfg.process_sort && !c->cfg.pipeline) ? 1 : 0;
   s.claim_chunks = c->cfg.claim_chunks;
   s.along_steps = c->cfg.along_steps;
   s.scoring = c->cfg.scoring;
@@ -2191,6 +2207,7 @@ extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long 
   s.view.status = &s.ctl->status;
   s.mode = GV_BATCHED;
   s.chunk = c->cfg.block_size;  // the non-basketizing kernel, one claim per block
+  s.adaptive_chunk = 0;
   s.claim_chunks = 0;
   s.low_water = static_cast<unsigned long long>(kStaticCap / 4);
   s.batch = std::min<unsigned long long>(s.batch, 64);

@@ -53,7 +53,7 @@ struct Ctl {
   unsigned cnt[2][3];        // queue fill per buffer parity and type
   unsigned prim_next;        // primaries handed out so far
   unsigned prim_begin, prim_count;
-  unsigned chunk_end[4];     // cumulative chunk counts: gamma, e-, e+, primaries
+  unsigned chunk_end[4];     // cumulative chunk counts in claim order: e+, e-, gamma, primaries
   unsigned claim;            // chunk claim counter
   unsigned blocks_done;
   int K;                     // steps per claimed track this generation

@@ -65,6 +65,7 @@ struct Ctl {
   unsigned max_in_flight;        // refill cap of this call (0: none)
   unsigned emax_bits;            // largest primary energy (FP32 bits), for the automatic cap
   unsigned long long gen;
+  unsigned long long loop_iter;  // bodies of the device-side generation loop run so far
   unsigned long long live_peak;
   unsigned long long counters[16];
   // split pipeline: requests of this generation, per key, and the claim /

@@ -629,6 +629,7 @@ template <typename R> __global__ void init_kernel(const DevState<R> *S) {
   c->status = 0;
   c->done = 0;
   c->gen = 0;
+  c->loop_iter = 0;
   c->live_peak = 0;
   c->ev_started = 0;
   c->ev_done = 0;
@@ -1367,6 +1368,7 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
   cudaGraphExec_t graph = nullptr;
+  int loop_graph = 0;  // graph holds the device-side generation loop
   Ctl *h_ctl = nullptr;  // pinned
   long long launches = 0;
   int last_status = 0;
@@ -1684,64 +1686,135 @@ template <typename R> DevState<R> make_state(Ctx *c) {
   return s;
 }
 
-template <typename R> int capture_graph(Ctx *c) {
-  if (c->graph) return GV_OK;
-  cudaGraph_t g;
-  CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+// The gate at the end of every body of the device-side generation loop: it
+// keeps the loop running while the transport is not done.  The loop cannot
+// outrun its budget: after max_iter bodies the gate records GV_ERR_TIMEOUT,
+// marks the transport done and ends the loop (the generation budget itself
+// ends it earlier through plan_next).
+__global__ void loop_gate_kernel(Ctl *ctl, cudaGraphConditionalHandle h, unsigned long long max_iter) {
+  const unsigned long long it = ++ctl->loop_iter;
+  int stop = ctl->done;
+  if (!stop && it >= max_iter) {
+    if (ctl->status == 0) ctl->status = GV_ERR_TIMEOUT;
+    ctl->done = 1;
+    stop = 1;
+  }
+  cudaGraphSetConditional(h, stop ? 0u : 1u);
+}
+
+// Puts the persisting-L2 window on every kernel node of g.
+cudaError_t set_l2_window(const Ctx *c, cudaGraph_t g) {
+  size_t nn = 0;
+  cudaError_t e = cudaGraphGetNodes(g, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (e == cudaSuccess && nn) e = cudaGraphGetNodes(g, nodes.data(), &nn);
+  cudaKernelNodeAttrValue v{};
+  v.accessPolicyWindow.base_ptr = c->d_bins;
+  v.accessPolicyWindow.num_bytes = c->l2_window;
+  v.accessPolicyWindow.hitRatio = 1.0f;
+  v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+  v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+  for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
+    cudaGraphNodeType ty;
+    e = cudaGraphNodeGetType(nodes[i], &ty);
+    if (e == cudaSuccess && ty == cudaGraphNodeTypeKernel)
+      e = cudaGraphKernelNodeSetAttribute(nodes[i], cudaKernelNodeAttributeAccessPolicyWindow, &v);
+  }
+  return e;
+}
+
+// The generations of one graph body, recorded on the (capturing) stream.
+template <typename R> cudaError_t record_generations(Ctx *c) {
   const DevState<R> *S = reinterpret_cast<const DevState<R> *>(c->d_state);
   if (c->cfg.pipeline) {
     for (int i = 0; i < c->cfg.generations_per_graph; ++i) {
       along_kernel<R><<<c->grid, c->cfg.block_size, c->smem_bytes, c->stream>>>(S, i & 1);
       interact_kernel<R><<<c->grid_b, 256, 0, c->stream>>>(S, i & 1);
     }
-  } else {
-    const StepFn<R> step = pick_step_kernel<R>(c->cfg, c->geo.field_T != 0.0);
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    for (int i = 0; i < c->cfg.generations_per_graph; ++i) {
-      cudaLaunchConfig_t lc = {};
-      lc.gridDim = dim3(c->grid);
-      lc.blockDim = dim3(c->cfg.block_size);
-      lc.dynamicSmemBytes = c->smem_bytes;
-      lc.stream = c->stream;
-      lc.attrs = attr;
-      lc.numAttrs = (c->cfg.pdl && i > 0) ? 1 : 0;  // overlap with the previous generation's tail
-      const int parity = i & 1;
-      if (cudaLaunchKernelEx(&lc, step, static_cast<const DevState<R> *>(S), parity) != cudaSuccess) {
-        cudaGraph_t junk = nullptr;
-        cudaStreamEndCapture(c->stream, &junk);
-        if (junk) cudaGraphDestroy(junk);
-        return GV_ERR_CUDA;
-      }
-    }
+    return cudaGetLastError();
   }
-  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-  if (e != cudaSuccess) return GV_ERR_CUDA;
-  if (c->l2_window) {  // the window rides on every captured step launch
-    size_t nn = 0;
-    e = cudaGraphGetNodes(g, nullptr, &nn);
-    std::vector<cudaGraphNode_t> nodes(nn);
-    if (e == cudaSuccess && nn) e = cudaGraphGetNodes(g, nodes.data(), &nn);
-    cudaKernelNodeAttrValue v{};
-    v.accessPolicyWindow.base_ptr = c->d_bins;
-    v.accessPolicyWindow.num_bytes = c->l2_window;
-    v.accessPolicyWindow.hitRatio = 1.0f;
-    v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-    v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
-    for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
-      cudaGraphNodeType ty;
-      e = cudaGraphNodeGetType(nodes[i], &ty);
-      if (e == cudaSuccess && ty == cudaGraphNodeTypeKernel)
-        e = cudaGraphKernelNodeSetAttribute(nodes[i], cudaKernelNodeAttributeAccessPolicyWindow, &v);
-    }
-    if (e != cudaSuccess) {
-      cudaGraphDestroy(g);
-      return GV_ERR_CUDA;
-    }
+  const StepFn<R> step = pick_step_kernel<R>(c->cfg, c->geo.field_T != 0.0);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  for (int i = 0; i < c->cfg.generations_per_graph; ++i) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(c->grid);
+    lc.blockDim = dim3(c->cfg.block_size);
+    lc.dynamicSmemBytes = c->smem_bytes;
+    lc.stream = c->stream;
+    lc.attrs = attr;
+    lc.numAttrs = (c->cfg.pdl && i > 0) ? 1 : 0;  // overlap with the previous generation's tail
+    const int parity = i & 1;
+    const cudaError_t e = cudaLaunchKernelEx(&lc, step, static_cast<const DevState<R> *>(S), parity);
+    if (e != cudaSuccess) return e;
   }
-  e = cudaGraphInstantiate(&c->graph, g, 0);
-  cudaGraphDestroy(g);
+  return cudaSuccess;
+}
+
+// The transport as one graph: a device-side while loop whose body runs
+// generations_per_graph generations and then the gate, so the host launches
+// once and waits once, and no body starts after the plan that ends the
+// transport (the rest of its own body returns at once).
+template <typename R> int capture_loop_graph(Ctx *c) {
+  cudaGraph_t outer = nullptr;
+  if (cudaGraphCreate(&outer, 0) != cudaSuccess) return GV_ERR_CUDA;
+  cudaGraphConditionalHandle h;
+  cudaGraphNodeParams np = {};
+  cudaGraphNode_t node;
+  if (cudaGraphConditionalHandleCreate(&h, outer, 1u, cudaGraphCondAssignDefault) != cudaSuccess) {
+    cudaGraphDestroy(outer);
+    return GV_ERR_CUDA;
+  }
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  if (cudaGraphAddNode(&node, outer, nullptr, nullptr, 0, &np) != cudaSuccess) {
+    cudaGraphDestroy(outer);
+    return GV_ERR_CUDA;
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  if (cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+      cudaSuccess) {
+    cudaGraphDestroy(outer);
+    return GV_ERR_CUDA;
+  }
+  cudaError_t e = record_generations<R>(c);
+  const unsigned long long max_iter =
+      static_cast<unsigned long long>(c->cfg.max_generations) / c->cfg.generations_per_graph + 2;
+  if (e == cudaSuccess) {
+    loop_gate_kernel<<<1, 1, 0, c->stream>>>(c->d_ctl, h, max_iter);
+    e = cudaGetLastError();
+  }
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(c->stream, &captured);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess && c->l2_window) e = set_l2_window(c, body);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, outer, 0);
+  cudaGraphDestroy(outer);
+  if (e != cudaSuccess) {
+    c->graph = nullptr;
+    return GV_ERR_CUDA;
+  }
+  c->loop_graph = 1;
+  return GV_OK;
+}
+
+template <typename R> int capture_graph(Ctx *c) {
+  if (c->graph) return GV_OK;
+  c->loop_graph = 0;
+  if (capture_loop_graph<R>(c) == GV_OK) return GV_OK;
+  cudaGetLastError();  // no conditional nodes in this runtime: generations looped by the host
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = record_generations<R>(c);
+  const cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess && c->l2_window) e = set_l2_window(c, g);  // the window rides on every step launch
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) c->graph = nullptr;
   return e == cudaSuccess ? GV_OK : GV_ERR_CUDA;
 }
 
@@ -1850,7 +1923,19 @@ int run_transport(Ctx *c, const gv_primary *p, long long n, long long n_events, 
   long long launches = (s.max_in_flight < 0 && n > 0) ? 2 : 1;
   int between = 1;
   double kernel_ms = 0.0;
-  for (;;) {
+  if (c->loop_graph) {  // one launch: the device-side loop runs until the transport is done
+    CK(cudaEventRecord(c->t0, c->stream));
+    CK(cudaGraphLaunch(c->graph, c->stream));
+    CK(cudaEventRecord(c->t1, c->stream));
+    CK(cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->t0, c->t1));
+    kernel_ms = ms;
+    launches += static_cast<long long>(c->h_ctl->loop_iter) *
+                (c->cfg.generations_per_graph * (c->cfg.pipeline ? 2 : 1) + 1);
+  }
+  for (; !c->loop_graph;) {
     CK(cudaEventRecord(c->t0, c->stream));
     for (int i = 0; i < between; ++i) CK(cudaGraphLaunch(c->graph, c->stream));
     CK(cudaEventRecord(c->t1, c->stream));
@@ -2167,6 +2252,7 @@ __global__ void static_begin_kernel(DevState<float> s, DevState<float> *dst) {
   c->status = 0;
   c->done = 0;
   c->gen = 0;
+  c->loop_iter = 0;
   c->live_peak = 0;
   c->ev_started = 0;
   c->ev_done = 0;

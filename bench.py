@@ -229,6 +229,9 @@ def main():
                     help="events per step (profiling of small cases only)")
     ap.add_argument("--capacity", type=int, default=1 << 23, help="track queue capacity per type")
     ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="relaunch the generation graph from the host (device_loop=0): the same kernels, "
+                         "in graphs that ncu can profile kernel by kernel")
     ap.add_argument("--comparator-events", type=int, default=200,
                     help="events of the one-event-per-launch comparators")
     args = ap.parse_args()
@@ -251,7 +254,8 @@ def main():
     wl = _workload(rank)
     if args.events != N_EVENTS:
         wl = wl.subset(args.events)
-    ctx = gv.Context(wl, gv.gv_default_config(stack_capacity=args.capacity))
+    ctx = gv.Context(wl, gv.gv_default_config(stack_capacity=args.capacity,
+                                              device_loop=0 if args.host_loop else 1))
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     prim_d = torch.from_numpy(wl.primaries.view(np.uint8).copy()).to(dev)

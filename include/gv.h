@@ -165,6 +165,11 @@ typedef struct {
   int pdl;                    /* 1 (default): successive step kernels of a graph use programmatic dependent
                                  launch: a generation's blocks stage their tables while the previous
                                  generation drains, and wait for it before reading its plan */
+  int device_loop;            /* 1 (default): the transport is one graph launch whose conditional WHILE
+                                 node repeats generations_per_graph generations until the plan marks it
+                                 done; 0: the host relaunches the generation graph and checks after
+                                 1, 2, 4, ... graphs (the same kernels; ncu profiles kernels only in
+                                 graphs without conditional nodes) */
 } gv_config;
 
 /* A primary track; layout shared with the seeded input generator.  Its random

@@ -1432,6 +1432,7 @@ int validate_cfg(const gv_config &c) {
   if (c.l2_persist < 0 || c.l2_persist > 1) return GV_ERR_BAD_ARG;
   if (c.local_stack < 0 || c.local_stack > 1) return GV_ERR_BAD_ARG;
   if (c.pdl < 0 || c.pdl > 1) return GV_ERR_BAD_ARG;
+  if (c.device_loop < 0 || c.device_loop > 1) return GV_ERR_BAD_ARG;
   if (c.pipeline < 0 || c.pipeline > 1 || (c.pipeline == 1 && c.scoring != 0)) return GV_ERR_BAD_ARG;
   return GV_OK;
 }
@@ -1804,7 +1805,7 @@ template <typename R> int capture_loop_graph(Ctx *c) {
 template <typename R> int capture_graph(Ctx *c) {
   if (c->graph) return GV_OK;
   c->loop_graph = 0;
-  if (capture_loop_graph<R>(c) == GV_OK) return GV_OK;
+  if (c->cfg.device_loop && capture_loop_graph<R>(c) == GV_OK) return GV_OK;
   cudaGetLastError();  // no conditional nodes in this runtime: generations looped by the host
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
@@ -2006,6 +2007,7 @@ int gv_default_config(gv_config *cfg) {
   cfg->pipeline = 0;
   cfg->local_stack = 1;
   cfg->pdl = 1;
+  cfg->device_loop = 1;
   return GV_OK;
 }
 

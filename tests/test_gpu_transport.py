@@ -189,7 +189,7 @@ def test_integer_counts_invariant_to_launch_shape(gvmod):
               dict(local_stack=1), dict(local_stack=1, steps_per_claim=3, block_size=64),
               dict(local_stack=1, tail_steps_per_claim=16, tail_threshold=1 << 40, scoring=1),
               dict(pdl=1), dict(pdl=1, process_sort=0, generations_per_graph=4),
-              dict(device_loop=0), dict(device_loop=0, generations_per_graph=3, pipeline=1)]
+              dict(device_loop=0), dict(device_loop=0, generations_per_graph=6, pipeline=1)]
     for kw in shapes:
         ctx = _ctx(gvmod, wl, per_event_counts=1, **kw)
         r = ctx.transport(per_event=True)

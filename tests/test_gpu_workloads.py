@@ -188,3 +188,57 @@ def test_pair_sampler_timing_rejection_vs_tables(gvmod):
         assert 1.0 <= trials < 1.6
     ctx.close()
     _report("pair_sampler_rejection_vs_tables", samples=n, per_energy_MeV=res)
+
+
+def _cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def test_oracle_timing_on_host(oracle_mod):
+    """The FP64 oracle timed on the host cores of the GPU machine: configs 1, 2
+    and 4 in full and configs 3 and 5 on event subsets, with every core and
+    with one thread (one thread on subsets); steps/s of a subset stands for
+    the whole workload (labelled).  It uses no GPU; it is marked with the GPU
+    tests because its numbers are about the GPU machine's host."""
+    import time
+    nthr = NTHR
+    plan = [  # (workload, events with every core, events with one thread)
+        (W.PHOTON_SLAB, None, 20_000),
+        (W.PBPS_1GEV, None, 200),
+        (W.PBPS_MIXED, 512, 64),
+        (W.PBPS_10GEV, None, 100),
+        (W.WSI_100GEV, 160, 8),
+    ]
+    rows = {}
+    for name, n_all, n_one in plan:
+        wl = W.standard(name)
+        row = {}
+        for label, n, thr in (("all_cores", n_all, nthr), ("one_thread", n_one, 1)):
+            sub = wl.subset(n) if n else wl
+            o = oracle_mod.Oracle(sub)
+            t = time.perf_counter()
+            r = o.transport(n_threads=thr)
+            dt = time.perf_counter() - t
+            steps = int(r["counts"][:, 0].sum())
+            assert steps > 0
+            row[label] = {"threads": thr, "events": sub.n_events, "of_events": wl.n_events,
+                          "seconds": dt, "steps": steps, "steps_per_s": steps / dt,
+                          "events_per_s": sub.n_events / dt}
+        rows[name] = row
+    _report("oracle_timing_host", cpu=_cpu_model(), cores=nthr, configs=rows)

@@ -602,8 +602,10 @@ template <typename R> __device__ void plan_next(const DevState<R> *S, int pn) {
   c->chunk_end[1] = c->chunk_end[0] + (n1 + B - 1) / B;
   c->chunk_end[2] = c->chunk_end[1] + (n0 + B - 1) / B;
   c->chunk_end[3] = c->chunk_end[2] + (inj + B - 1) / B;
-  // long claims only in the true tail (every primary injected, few tracks
-  // left); a small population at the start grows fastest with short claims
+  // long claims (K_tail rounds) once every primary is injected and few
+  // tracks are live: in the tail, and at the start of a batch injected at
+  // once, where the block stack keeps a claim's secondaries stepping in the
+  // block (one-round claims there measured slower on small batches)
   c->K = (c->prim_next == S->n_prim && live + inj < S->tail_threshold) ? S->K_tail : S->K_bulk;
   c->cnt[pn ^ 1][0] = c->cnt[pn ^ 1][1] = c->cnt[pn ^ 1][2] = 0;
   c->claim = 0;

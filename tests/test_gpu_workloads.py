@@ -78,6 +78,22 @@ def test_precision_study_10GeV(gvmod, oracle_mod):
     _report("precision_10GeV_PbPS", **out)
 
 
+def test_photon_slab_measured(gvmod):
+    """Config 1 (1e5 photons of 1 MeV in 10 cm of water-like material) timed
+    in both precisions; its parity is tested with the transmission pin."""
+    wl = W.standard(W.PHOTON_SLAB)
+    out = {}
+    for prec, name in ((1, "fp64"), (0, "mixed")):
+        r = _run(gvmod, wl, precision=prec)
+        c = r["counters"]
+        out[name] = {"kernel_ms": r["kernel_ms"], "steps": c["steps"],
+                     "steps_per_s": c["steps"] / (r["kernel_ms"] / 1e3),
+                     "photons_per_s": wl.n_events / (r["kernel_ms"] / 1e3),
+                     "unscattered": c["unscattered"] / wl.n_events}
+    assert abs(out["fp64"]["unscattered"] - out["mixed"]["unscattered"]) < 0.01
+    _report("gamma1MeV_water10cm", events=wl.n_events, **out)
+
+
 def test_pbps_1GeV_measured(gvmod, oracle_mod):
     wl = W.standard(W.PBPS_1GEV)
     r = _run(gvmod, wl)

@@ -116,6 +116,22 @@ def test_mixed_showers_statistical_parity_1GeV(gvmod, oracle_mod):
     assert abs(steps_g / steps_o - 1) < 0.01
 
 
+def test_mixed_showers_statistical_parity_10GeV(gvmod, oracle_mod):
+    """The benchmark's energy with enough showers (65536) that 0.5 % is a
+    3-combined-sigma bound on the layers near the maximum, in the benchmark
+    launch shape."""
+    wl = W.pbps_electrons(65_536, 10_000.0)
+    ctx = _ctx(gvmod, wl, stack_capacity=1 << 23)
+    r = ctx.transport()
+    assert r["status"] == 0
+    ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
+    pull, nbig = layer_parity(wl, r["edep"], ref["edep"])
+    assert nbig >= 5, nbig  # the 0.5% criterion is exercised
+    steps_g = r["counters"]["steps"]
+    steps_o = ref["counts"][:, 0].sum()
+    assert abs(steps_g / steps_o - 1) < 0.01
+
+
 def test_energy_and_charge_conservation_mixed(gvmod):
     wl = W.pbps_electrons(2000, 10_000.0)
     ctx = _ctx(gvmod, wl, per_event_counts=1)

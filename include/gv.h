@@ -135,7 +135,7 @@ typedef struct {
   long long stack_capacity;   /* tracks per particle-type queue (each double-buffered) */
   long long refill_low_water; /* inject primaries while fewer live tracks than this */
   long long refill_batch;     /* at most this many primaries per generation */
-  int generations_per_graph;  /* generations captured in one CUDA graph (even) */
+  int generations_per_graph;  /* generations per body of the graph loop (even) */
   long long max_generations;  /* budget; exceeded -> GV_ERR_TIMEOUT */
   int per_event_counts;       /* 1: keep GV_NCOUNT counters per event (slower) */
   int process_sort;           /* 1: re-basket interacting tracks by process in each block */

@@ -1,14 +1,17 @@
 // gv_transport.cu -- the stepping loop of GeantV (Sec. 2.1.2, Fig.
 // "simulation stages") as a persistent, chunk-claiming CUDA kernel driven
-// generation by generation from a captured CUDA graph, plus the C ABI.
+// generation by generation from a captured CUDA graph (a device-side while
+// loop over bodies of generations), plus the C ABI.
 //
 // One generation: every live track of the three per-type queues (and the
-// primaries injected by the refill plan) is claimed in chunks of one block,
-// stepped K times, and written back -- survivors and secondaries appended to
-// the other parity's queues with warp-aggregated atomics (the basketizer of
-// scheduler v3, Sec. 2.1.1).  The last block to finish writes the plan of
-// the next generation: queue chunk ranges, primaries to inject (the event
-// server refill, bounded by a live-track budget) and the steps per claim.
+// primaries injected by the refill plan) is claimed in chunks (a block's
+// worth, fewer when few tracks are live; positrons, electrons, photons,
+// primaries in that order), stepped K times, and written back -- survivors
+// and secondaries appended to the other parity's queues with warp-aggregated
+// atomics (the basketizer of scheduler v3, Sec. 2.1.1).  The last block to
+// finish writes the plan of the next generation: queue chunk ranges and
+// claim size, primaries to inject (the event server refill, bounded by a
+// live-track budget) and the steps per claim.
 #include <cuda_runtime.h>
 
 #include <algorithm>

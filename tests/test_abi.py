@@ -90,6 +90,16 @@ def test_argument_validation_without_gpu(lib):
     assert lib.gv_setup(C.byref(h), mats, 1, C.byref(geo2), C.byref(cuts), None) == -1
     cfg = gv.gv_default_config(block_size=100)
     assert lib.gv_setup(C.byref(h), mats, 1, C.byref(geo), C.byref(cuts), C.byref(cfg)) == -1
+    # every knob out of its range is refused before any CUDA call
+    for bad_knob in (dict(precision=2), dict(mode=3), dict(block_size=32), dict(block_size=1024),
+                     dict(blocks_per_sm=0), dict(steps_per_claim=0), dict(tail_steps_per_claim=5000),
+                     dict(stack_capacity=100), dict(refill_batch=0), dict(refill_low_water=-1),
+                     dict(generations_per_graph=3), dict(generations_per_graph=0), dict(max_generations=0),
+                     dict(max_events_in_flight=-2), dict(claim_chunks=2), dict(along_steps=0),
+                     dict(along_steps=65), dict(scoring=2), dict(l2_persist=-1), dict(local_stack=2),
+                     dict(pdl=2), dict(device_loop=2), dict(pipeline=2), dict(pipeline=1, scoring=1)):
+        cfg = gv.gv_default_config(**bad_knob)
+        assert lib.gv_setup(C.byref(h), mats, 1, C.byref(geo), C.byref(cuts), C.byref(cfg)) == -1, bad_knob
     assert lib.gv_transport(None, None, 0, 1, 0, None, None) == -1
     assert lib.gv_unit_philox(None, None, None, 0, None) == 0
     assert lib.gv_unit_philox(None, None, None, -1, None) == -1

@@ -90,6 +90,42 @@ def test_argument_validation_without_gpu(lib):
     assert lib.gv_setup(C.byref(h), mats, 1, C.byref(geo2), C.byref(cuts), None) == -1
     cfg = gv.gv_default_config(block_size=100)
     assert lib.gv_setup(C.byref(h), mats, 1, C.byref(geo), C.byref(cuts), C.byref(cfg)) == -1
+    # every malformed material, geometry or cut is refused before any CUDA call
+    def mat_case(**kw):
+        m = (gv.gv_material * 1)()
+        C.memmove(C.byref(m[0]), C.byref(mats[0]), C.sizeof(gv.gv_material))
+        for k, v in kw.items():
+            if k in ("Z", "A", "w"):
+                getattr(m[0], k)[0] = v
+            else:
+                setattr(m[0], k, v)
+        return m
+
+    for kw in (dict(n_elem=0), dict(n_elem=1000), dict(rho=0.0), dict(rho=float("nan")), dict(I_eV=-1.0),
+               dict(Z=0.0), dict(A=0.0), dict(w=0.0)):
+        assert lib.gv_setup(C.byref(h), mat_case(**kw), 1, C.byref(geo), C.byref(cuts), None) == -1, kw
+    assert lib.gv_setup(C.byref(h), mats, 0, C.byref(geo), C.byref(cuts), None) == -1
+    assert lib.gv_setup(C.byref(h), mats, 5, C.byref(geo), C.byref(cuts), None) == -1  # > GV_MAX_MAT
+
+    def geo_case(**kw):
+        g = gv.gv_layers()
+        C.memmove(C.byref(g), C.byref(geo), C.sizeof(gv.gv_layers))
+        for k, v in kw.items():
+            if k in ("sub_thick_cm", "sub_mat"):
+                getattr(g, k)[0] = v
+            else:
+                setattr(g, k, v)
+        return g
+
+    for kw in (dict(n_layers=0), dict(n_sub=0), dict(n_sub=9), dict(sub_thick_cm=0.0), dict(sub_thick_cm=-1.0),
+               dict(sub_mat=1), dict(sub_mat=-1), dict(nx_cells=-1), dict(nx_cells=4, ny_cells=4),
+               dict(nx_cells=4, ny_cells=0, half_x_cm=5.0, half_y_cm=5.0), dict(field_T=1e5),
+               dict(field_axis=3), dict(field_axis=-1)):
+        g = geo_case(**kw)
+        assert lib.gv_setup(C.byref(h), mats, 1, C.byref(g), C.byref(cuts), None) == -1, kw
+    for bad_cuts in (gv.gv_cuts(1.0, 1.0, float("nan"), 63), gv.gv_cuts(1e-4, 1.0, 1e-3, 63),
+                     gv.gv_cuts(1.0, 1e-4, 1e-3, 63)):
+        assert lib.gv_setup(C.byref(h), mats, 1, C.byref(geo), C.byref(bad_cuts), None) == -1
     # every knob out of its range is refused before any CUDA call
     for bad_knob in (dict(precision=2), dict(mode=3), dict(block_size=32), dict(block_size=1024),
                      dict(blocks_per_sm=0), dict(steps_per_claim=0), dict(tail_steps_per_claim=5000),

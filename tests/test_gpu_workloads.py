@@ -79,8 +79,9 @@ def test_precision_study_10GeV(gvmod, oracle_mod):
 
 
 def test_photon_slab_measured(gvmod):
-    """Config 1 (1e5 photons of 1 MeV in 10 cm of water-like material) timed
-    in both precisions; its parity is tested with the transmission pin."""
+    """The photon slab (1e5 photons of 1 MeV in 10 cm of water-like
+    material) timed in both precisions; its parity is tested with the
+    transmission pin."""
     wl = W.standard(W.PHOTON_SLAB)
     out = {}
     for prec, name in ((1, "fp64"), (0, "mixed")):
@@ -227,11 +228,12 @@ def _cpu_model() -> str:
 
 
 def test_oracle_timing_on_host(oracle_mod):
-    """The FP64 oracle timed on the host cores of the GPU machine: configs 1, 2
-    and 4 in full and configs 3 and 5 on event subsets, with every core and
-    with one thread (one thread on subsets); steps/s of a subset stands for
-    the whole workload (labelled).  It uses no GPU; it is marked with the GPU
-    tests because its numbers are about the GPU machine's host."""
+    """The FP64 oracle timed on the host cores of the machine that holds the
+    GPU: the photon slab, the 1 GeV and the 10 GeV electron workloads in full
+    and the mixed-type and 100 GeV W/Si workloads on event subsets, with every
+    core and with one thread (one thread on subsets); steps/s of a subset
+    stands for the whole workload (labelled).  It uses no GPU; it is marked
+    with the GPU tests because its numbers are about that machine's host."""
     import time
     nthr = NTHR
     plan = [  # (workload, events with every core, events with one thread)

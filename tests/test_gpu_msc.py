@@ -89,6 +89,19 @@ def test_fp64_field_showers_follow_oracle_event_by_event(gvmod, oracle_mod):
     assert np.abs(r["edep"][same] - ref["edep"][same]).max() < 1e-9 * 1000.0
 
 
+def test_fp64_all_options_follow_oracle_event_by_event(gvmod, oracle_mod):
+    """Every option at once in FP64 -- multiple scattering, a 4 T field,
+    rejection samplers and the integral approach -- on the TestEm3 layout:
+    the histories coincide with the oracle's event by event."""
+    wl = W.with_integral(W.with_rejection(W.with_msc(W.with_field(W.pblar_testem3(200, 1000.0), 4.0, 1))))
+    r = _run(gvmod, wl, precision=1, per_event_counts=1)
+    ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
+    same = np.all(r["counts"][:, :11] == ref["counts"][:, :11], axis=1)
+    assert same.mean() >= 0.9, same.mean()
+    assert np.abs(r["edep"][same] - ref["edep"][same]).max() < 1e-9 * 1000.0
+    assert np.abs(_conservation(wl, r)).max() < 1e-9
+
+
 def test_testem3_field_and_msc_paper_conditions(gvmod, oracle_mod):
     """The paper's TestEm3 conditions as far as this physics list goes: 50 x
     (2.3 mm Pb + 5.7 mm LAr), 10 GeV e-, 4 T transverse field, multiple

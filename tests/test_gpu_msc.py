@@ -102,6 +102,24 @@ def test_fp64_all_options_follow_oracle_event_by_event(gvmod, oracle_mod):
     assert np.abs(_conservation(wl, r)).max() < 1e-9
 
 
+def test_mixed_all_options_cells_statistical(gvmod, oracle_mod):
+    """Every option at once in mixed precision on the segmented W/Si
+    calorimeter (cells scored at the helix midpoint): per-layer means and the
+    lateral profile against the oracle."""
+    wl = W.with_integral(W.with_rejection(W.with_msc(W.with_field(W.wsi_cells(400, 20_000.0), 4.0, 1))))
+    r = _run(gvmod, wl, stack_capacity=1 << 23, per_event_counts=1)
+    ref = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
+    layer_parity(wl, r["edep"], ref["edep"])
+    assert np.abs(_conservation(wl, r)).max() < 1e-5
+    per_layer = r["edep"].reshape(wl.n_events, wl.n_layers, -1).sum((0, 2))
+    assert np.allclose(r["cell"].sum((1, 2)), per_layer, rtol=1e-9)
+
+    def rings(cell):
+        tot = cell.sum()
+        return np.array([cell[:, 16 - k:16 + k, 16 - k:16 + k].sum() / tot for k in (2, 4, 8)])
+    assert np.abs(rings(r["cell"]) - rings(ref["cell"])).max() < 0.005
+
+
 def test_testem3_field_and_msc_paper_conditions(gvmod, oracle_mod):
     """The paper's TestEm3 conditions as far as this physics list goes: 50 x
     (2.3 mm Pb + 5.7 mm LAr), 10 GeV e-, 4 T transverse field, multiple

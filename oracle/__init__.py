@@ -52,7 +52,7 @@ class OrSetup(C.Structure):
                 ("half_x", C.c_double), ("half_y", C.c_double), ("nx", C.c_int), ("ny", C.c_int),
                 ("gamma_cut", C.c_double), ("e_cut", C.c_double), ("track_cut", C.c_double),
                 ("process_mask", C.c_uint), ("field_T", C.c_double), ("field_axis", C.c_int),
-                ("reject_min", C.c_double * 6)]
+                ("reject_min", C.c_double * 6), ("exact", C.c_int)]
 
 
 def _load():
@@ -105,6 +105,12 @@ def _load():
             lib.or_sigma_max.argtypes = [p, i, i, d]
             lib.or_reject_sample.restype = d
             lib.or_reject_sample.argtypes = [p, i, d, p, C.POINTER(d), C.POINTER(i)]
+            lib.or_exact_sample.restype = d
+            lib.or_exact_sample.argtypes = [p, i, d, p, C.POINTER(d), C.POINTER(i)]
+            lib.or_range_at.restype = d
+            lib.or_range_at.argtypes = [p, i, i, d]
+            lib.or_eloss_exact.restype = d
+            lib.or_eloss_exact.argtypes = [p, i, i, d, d]
             lib.or_safety.restype = d
             lib.or_safety.argtypes = [p, p, i]
             lib.or_msc_theta0.restype = d
@@ -114,6 +120,7 @@ def _load():
             lib.or_field_step_limit.argtypes = [p, i, d, p]
             lib.or_helix.argtypes = [p, i, d, d, p, p, p]
             lib.or_transport.argtypes = [p, p, C.c_long, C.c_long, C.c_uint64, p, p, p, p, i]
+            lib.or_transport_events.argtypes = [p, p, C.c_long, C.c_long, C.c_long, C.c_uint64, p, p, p, p, i]
             _lib = lib
     return _lib
 
@@ -137,10 +144,17 @@ def klein_nishina_e(k: float) -> float:
 
 
 class Oracle:
-    """One oracle context: materials, geometry, cuts, FP64 tables."""
+    """One oracle context: materials, geometry, cuts, FP64 tables.
 
-    def __init__(self, wl):
+    exact=True selects the untabulated transport: cross sections from their
+    formulas at each track's own energy, range and continuous loss by
+    quadrature and root finding, every final state by rejection from its
+    DCS.  The default transport interpolates the stepping tables and samples
+    the sampling tables, as the paper's method does (Sec. 3.5, Sec. 6.6)."""
+
+    def __init__(self, wl, exact: bool = False):
         self.wl = wl
+        self.exact = bool(exact)
         lib = _load()
         s = OrSetup()
         s.n_mat = len(wl.materials)
@@ -163,6 +177,7 @@ class Oracle:
         s.field_T, s.field_axis = wl.field_T, wl.field_axis
         for m in range(6):
             s.reject_min[m] = wl.reject_min[m] if wl.reject_min is not None else math.inf
+        s.exact = 1 if exact else 0
         self._setup = s
         h = C.c_void_p()
         rc = lib.or_create(C.byref(s), C.byref(h))
@@ -272,6 +287,22 @@ class Oracle:
         v = self.lib.or_reject_sample(self.h, model, E, _ptr(rr), C.byref(xi), C.byref(tr))
         return v, xi.value, tr.value
 
+    def exact_sample(self, model: int, E: float, rng) -> tuple:
+        """(physical variable, proposal uniform, trials) from the exact sampler of
+        any of the six models."""
+        rr = np.ascontiguousarray(rng, dtype=np.uint32)
+        xi, tr = C.c_double(), C.c_int()
+        v = self.lib.or_exact_sample(self.h, model, E, _ptr(rr), C.byref(xi), C.byref(tr))
+        return v, xi.value, tr.value
+
+    def range_at(self, ptype: int, mat: int, E: float) -> float:
+        """Untabulated range R(E) (node quadratures plus the partial interval)."""
+        return self.lib.or_range_at(self.h, ptype, mat, E)
+
+    def eloss_exact(self, ptype: int, mat: int, E: float, s: float) -> float:
+        """Untabulated post-step energy: the root of int_{E'}^{E} dE/S = s."""
+        return self.lib.or_eloss_exact(self.h, ptype, mat, E, s)
+
     # -- geometry
     def n_subtotal(self) -> int:
         return self.lib.or_n_subtotal(self.h)
@@ -320,7 +351,9 @@ class Oracle:
 
     # -- transport
     def transport(self, primaries=None, n_events=None, seed=None, n_threads: int = 1,
-                  cells: bool = True):
+                  cells: bool = True, first_event: int = 0):
+        """Transport the workload's primaries (rows: events first_event ..
+        first_event + n_events - 1, keyed by their global index)."""
         wl = self.wl
         p = wl.primaries if primaries is None else primaries
         p = np.ascontiguousarray(p)
@@ -332,9 +365,9 @@ class Oracle:
         cnt = np.zeros((n_events, NCOUNT), dtype=np.int64)
         ncell = wl.n_layers * wl.nx * wl.ny
         cell = np.zeros(max(ncell, 1)) if (cells and ncell > 0) else None
-        rc = self.lib.or_transport(self.h, _ptr(p), len(p), n_events, C.c_uint64(seed),
-                                   _ptr(edep), _ptr(cell) if cell is not None else None,
-                                   _ptr(esc), _ptr(cnt), n_threads)
+        rc = self.lib.or_transport_events(self.h, _ptr(p), len(p), first_event, n_events, C.c_uint64(seed),
+                                          _ptr(edep), _ptr(cell) if cell is not None else None,
+                                          _ptr(esc), _ptr(cnt), n_threads)
         if rc != 0:
             raise ValueError(f"or_transport failed ({rc})")
         res = {"edep": edep, "escape": esc, "counts": cnt}

@@ -6,12 +6,20 @@
  * baseline leg of the benchmark.  The product library never includes, links
  * or calls it, and it shares no code with the CUDA path.
  *
- * Everything is FP64, evaluated from the formulas on demand, in the order the
- * stepping stages of Sec. 2.1.2 name them.  Table nodes are the exact
- * quantities at the nodes of the logarithmic energy grid (the cross-section
- * tables the paper's profiles show as Spline::GetValueAt / G4PhysicsVector,
- * Sec. 6.6); alias sampling tables follow the "sampling tables" method of
- * Sec. 3.5 (alias method with a discrete intermediate variable).
+ * Everything is FP64, in the order the stepping stages of Sec. 2.1.2 name
+ * them.  Two transports share the stepping loop:
+ *  - tabulated (default), the paper's method: cross sections and ranges
+ *    interpolated linearly in ln E between table nodes that hold the exact
+ *    quantities at the nodes of the logarithmic energy grid (the tables the
+ *    paper's profiles show as Spline::GetValueAt / G4PhysicsVector, Sec.
+ *    6.6); final states from sampling tables (Sec. 3.5: the alias method with
+ *    a discrete intermediate variable), or by rejection where chosen;
+ *  - untabulated (or_setup.exact): cross sections from their formulas at the
+ *    track's own energy, the range by quadrature of 1/S from the grid node
+ *    below, the post-step energy as the root of int_{E'}^{E} dE/S = s
+ *    (Newton on the quadrature, bracketed), and every final state by
+ *    rejection from its differential cross section.  It measures what the
+ *    tables cost.
  *
  * Parity status of each function is stated beside it; "pinned" means a test
  * in tests/test_oracle_pins.py checks it against something other than itself.
@@ -79,6 +87,11 @@ struct or_ctx {
   double smax[2][OR_MAX_MAT][GRID_N];
   oalias alias[OR_NMODEL];
   double gl_x[16], gl_w[16];
+  /* untabulated mode: the range gained across each grid interval, and the
+   * energies where S(E) has a kink, per charged type (0 e-, 1 e+) */
+  double dR[2][OR_MAX_MAT][GRID_N];
+  double kink[2][OR_MAX_MAT][3];
+  double gl6_x[6], gl6_w[6];
 };
 
 /* ------------------------------------------------------------------ */
@@ -157,7 +170,9 @@ double or_klein_nishina_e(double k) {
 }
 
 /* Sauter-type K-shell photoabsorption x 5/4 for all shells, per atom.
- * Parity unpinned beyond its scaling laws (no worked value in the paper). */
+ * Pinned: the Born limit of Stobbe's exact K-shell cross section (whose
+ * normalisation is pinned by the hydrogen threshold value), and the size in
+ * water against Hubbell & Seltzer's mu_en/rho at 10-20 keV. */
 static double photo_atom(double Z, double k) {
   double sT = 8.0 * PI * RE * RE / 3.0;
   double a4 = ALPHA * ALPHA * ALPHA * ALPHA;
@@ -225,8 +240,10 @@ static double density_effect(const omat *o, double T) {
 }
 
 /* Restricted collision stopping power (Berger-Seltzer, ICRU 37) with cut
- * Tc.  Pinned: ESTAR unrestricted value for water at 100 keV, and the
- * derivative w.r.t. the cut equals Tc x the Moller / Bhabha DCS. */
+ * Tc.  Pinned: ESTAR values for water (e-); both branches equal the
+ * unrestricted ICRU 37 formulas (F+ and F-) once the cut is above the
+ * largest transfer; the derivative w.r.t. the cut equals Tc x the Moller /
+ * Bhabha DCS. */
 static double dedx_col(const omat *o, int positron, double T, double Tc) {
   double tau = T / ME, g = tau + 1.0, b2 = 1.0 - 1.0 / (g * g);
   double Im = o->I / ME;
@@ -580,9 +597,70 @@ double or_reject_sample(const or_ctx *c, int model, double E, const uint32_t rng
   return v;
 }
 
+/* Exact samplers of the remaining models, by rejection from their DCS with
+ * the trial stream of or_reject_sample (block 3 + j/2, at most
+ * EXACT_MAX_TRIALS trials):
+ *   Moller   eps = T_delta/T in [x_c, 1/2], proposal density 1/eps^2,
+ *            accept eps^2 dsigma/deps / (2 + C1/4): dropping the two terms
+ *            with -C2 (C2 >= 0) leaves C1 eps^2 + 1 + eps^2/(1-eps)^2, at
+ *            most C1/4 + 2 for eps <= 1/2
+ *   Bhabha   eps in [x_c, 1], proposal 1/eps^2, accept beta^2 eps^2
+ *            dsigma/deps = 1 - beta^2 eps P(eps), P = B1 - B2 eps + B3 eps^2
+ *            - B4 eps^3: P' < 0 on [0, 1] (its discriminant is negative) and
+ *            P(1) = 2y(1 + y + y^2) > 0, so the ratio lies in [0, 1]
+ *   annih.   softer photon fraction eps in [eps_min, 1/2], proposal 1/eps,
+ *            accept eps (S(eps) + S(1-eps)) / M, S(x) = -a + b/x - 1/x^2,
+ *            a = (g+1)^2, b = g^2 + 4g + 1: eps S(eps) <= b - 2 sqrt(a) and
+ *            eps S(1-eps) <= (2b - 4 - a)/2 for eps <= 1/2, so
+ *            M = 1.5 g^2 + 5 g - 2.5 */
+#define EXACT_MAX_TRIALS 4096
+
+static double exact_other(const or_ctx *c, int model, double E, const uint32_t rng[5], double *xi_out,
+                          int *trials) {
+  const double cut = model_cut(c, model);
+  const double g = E / ME + 1.0, b2 = 1.0 - 1.0 / (g * g);
+  double v = 0.0, xi = 0.0;
+  int j;
+  uint32_t w[4] = {0, 0, 0, 0};
+  for (j = 0; j < EXACT_MAX_TRIALS; ++j) {
+    if ((j & 1) == 0) {
+      const uint32_t ctr[4] = {rng[0], rng[1], rng[2], REJ_BLOCK0 + (uint32_t)(j >> 1)};
+      const uint32_t key[2] = {rng[3], rng[4]};
+      or_philox4x32_10(ctr, key, w);
+    }
+    xi = u24(w[2 * (j & 1)]);
+    const double ua = u24(w[2 * (j & 1) + 1]);
+    double f;
+    if (model == OR_M_MOLLER) {
+      const double xc = cut / E;
+      v = xc / (1.0 - xi * (1.0 - 2.0 * xc));
+      const double C1 = ((g - 1.0) / g) * ((g - 1.0) / g);
+      f = v * v * or_dcs(model, E, v, cut) / (2.0 + 0.25 * C1);
+    } else if (model == OR_M_BHABHA) {
+      const double xc = cut / E;
+      v = xc / (1.0 - xi * (1.0 - xc));
+      f = b2 * v * v * or_dcs(model, E, v, cut);
+    } else {
+      v = xi_to_var(OR_M_ANNIH, E, xi, cut);
+      f = v * or_dcs(model, E, v, cut) / (1.5 * g * g + 5.0 * g - 2.5);
+    }
+    if (ua <= f) break;
+  }
+  if (trials) *trials = j < EXACT_MAX_TRIALS ? j + 1 : EXACT_MAX_TRIALS;
+  if (xi_out) *xi_out = xi;
+  return v;
+}
+
+double or_exact_sample(const or_ctx *c, int model, double E, const uint32_t rng[5], double *xi_out,
+                       int *trials) {
+  if (or_has_rejection(model)) return or_reject_sample(c, model, E, rng, xi_out, trials);
+  return exact_other(c, model, E, rng, xi_out, trials);
+}
+
 /* The sampler the setup chooses for (model, E): rejection where it is built
  * and E >= reject_min[model], else the sampling tables (u3: their uniforms). */
 static double sample_var(const or_ctx *c, int model, double E, const double *u3, const uint32_t rng[5]) {
+  if (c->s.exact) return or_exact_sample(c, model, E, rng, NULL, NULL);
   if (or_has_rejection(model) && E >= c->s.reject_min[model]) return or_reject_sample(c, model, E, rng, NULL, NULL);
   return or_alias_sample(c, model, E, u3, NULL);
 }
@@ -647,8 +725,22 @@ static void build_tables(or_ctx *c) {
       double R = GRID_EMIN / or_dedx(c, t, m, GRID_EMIN);
       c->tab[t][qR][m][0] = R;
       for (int i = 0; i + 1 < GRID_N; ++i) {
-        R += inv_dedx_integral(c, t, m, or_grid_energy(i), or_grid_energy(i + 1));
+        const double d = inv_dedx_integral(c, t, m, or_grid_energy(i), or_grid_energy(i + 1));
+        c->dR[t - 1][m][i] = d;
+        R += d;
         c->tab[t][qR][m][i + 1] = R;
+      }
+      {  /* the kinks of S(E): restricted ionisation switching to its cut, the
+          * gamma cut, the onset of the density effect (sorted) */
+        const omat *o = &c->mat[m];
+        double *k = c->kink[t - 1][m];
+        k[0] = t == OR_POSITRON ? c->s.e_cut : 2.0 * c->s.e_cut;
+        k[1] = c->s.gamma_cut;
+        const double bg = exp(0.5 - log(o->plasma / o->I));
+        k[2] = ME * (sqrt(1.0 + bg * bg) - 1.0);
+        for (int a = 0; a < 3; ++a)
+          for (int b = a + 1; b < 3; ++b)
+            if (k[b] < k[a]) { double x = k[a]; k[a] = k[b]; k[b] = x; }
       }
       /* the running maximum of the node values of Sigma(E) */
       double run = 0.0;
@@ -677,11 +769,21 @@ static void grid_pos(double E, int *i, double *f) {
   *f = fr;
 }
 
+/* Cross sections: linear in ln E between the nodes.  The range: ln R linear
+ * in ln E (R a power of E within an interval).  The range's slope in ln E,
+ * E/S(E), grows by ~7 % across an interval, so R linear in ln E would give
+ * every step inside an interval the interval's mean slope, i.e. a stopping
+ * power off by up to +-3.6 % (the untabulated transport shows it as a
+ * +0.9 % deposit in the first layer of 1 GeV showers); in ln R that slope
+ * error is the curvature of ln R, a few 1e-4. */
+static int is_range(int type, int q) { return type != OR_GAMMA && q == (type == OR_ELECTRON ? 2 : 3); }
+
 double or_table_lookup(const or_ctx *c, int type, int q, int mat, double E) {
   int i;
   double f;
   grid_pos(E, &i, &f);
   const double *v = c->tab[type][q][mat];
+  if (is_range(type, q)) return exp(log(v[i]) + f * (log(v[i + 1]) - log(v[i])));
   return v[i] + f * (v[i + 1] - v[i]);
 }
 
@@ -699,14 +801,12 @@ double or_sigma_max(const or_ctx *c, int type, int mat, double E) {
 
 /* Continuous loss along a step s from kinetic energy E (charged types): the
  * post-step energy is the exact inverse of the interpolated range,
- * E' = R^-1(R(E) - s), with R piecewise linear in ln E between nodes. */
+ * E' = R^-1(R(E) - s), with ln R piecewise linear in ln E between nodes;
+ * below the first node R is linear in E. */
 double or_eloss(const or_ctx *c, int type, int mat, double E, double s) {
   int qR = type == OR_ELECTRON ? 2 : 3;
   const double *R = c->tab[type][qR][mat];
-  int i;
-  double f;
-  grid_pos(E, &i, &f);
-  double Rv = R[i] + f * (R[i + 1] - R[i]);
+  double Rv = or_table_lookup(c, type, qR, mat, E);
   if (s >= Rv) return 0.0;
   double r = Rv - s;
   if (r < R[0]) return GRID_EMIN * r / R[0];
@@ -715,8 +815,100 @@ double or_eloss(const or_ctx *c, int type, int mat, double E, double s) {
     int mid = (lo + hi) / 2;
     if (R[mid] <= r) lo = mid; else hi = mid;
   }
-  double le = log(GRID_EMIN) + (log(10.0) / GRID_PPD) * (lo + (r - R[lo]) / (R[lo + 1] - R[lo]));
+  double le = log(GRID_EMIN) +
+              (log(10.0) / GRID_PPD) * (lo + (log(r) - log(R[lo])) / (log(R[lo + 1]) - log(R[lo])));
   return exp(le);
+}
+
+/* ------------------------------------------------------------------ */
+/* untabulated range and continuous loss                               */
+/* ------------------------------------------------------------------ */
+/* integral of dE/S over [a, b] (a <= b inside one grid interval), split at
+ * the kinks of S, 6-point Gauss-Legendre in ln E on each piece (a grid
+ * interval spans ln 10 / 32 = 0.072 in ln E, over which 6 points leave an
+ * error far below 1e-12 of the integral) */
+static double quad_inv_dedx(const or_ctx *c, int type, int mat, double a, double b) {
+  if (!(b > a)) return 0.0;
+  double edge[5];
+  int ne = 0;
+  edge[ne++] = a;
+  const double *k = c->kink[type - 1][mat];
+  for (int j = 0; j < 3; ++j)
+    if (k[j] > a && k[j] < b) edge[ne++] = k[j];
+  edge[ne++] = b;
+  double sum = 0.0;
+  for (int j = 0; j + 1 < ne; ++j) {
+    const double la = log(edge[j]), lb = log(edge[j + 1]);
+    const double h = 0.5 * (lb - la), mid = 0.5 * (la + lb);
+    for (int i = 0; i < 6; ++i) {
+      const double E = exp(mid + h * c->gl6_x[i]);
+      sum += h * c->gl6_w[i] * E / or_dedx(c, type, mat, E);
+    }
+  }
+  return sum;
+}
+
+/* grid interval i with E_i <= E < E_{i+1} (clamped to the grid) */
+static int grid_interval(double E) {
+  int i = (int)floor((log(E) - log(GRID_EMIN)) / (log(10.0) / GRID_PPD));
+  if (i < 0) i = 0;
+  if (i > GRID_N - 2) i = GRID_N - 2;
+  while (i > 0 && or_grid_energy(i) > E) --i;
+  while (i < GRID_N - 2 && or_grid_energy(i + 1) <= E) ++i;
+  return i;
+}
+
+/* R(E) = Emin/S(Emin) + int_{Emin}^{E} dE/S: the node value (a sum of exact
+ * interval quadratures) plus the quadrature from the node up to E -- no
+ * interpolation */
+double or_range_at(const or_ctx *c, int type, int mat, double E) {
+  const int qR = type == OR_ELECTRON ? 2 : 3;
+  const double R0 = c->tab[type][qR][mat][0];
+  if (E <= GRID_EMIN) return E / GRID_EMIN * R0;
+  const int i = grid_interval(E);
+  return c->tab[type][qR][mat][i] + quad_inv_dedx(c, type, mat, or_grid_energy(i), E);
+}
+
+/* Post-step energy E' of a step s from E with range R_E = R(E): the root of
+ * int_{E'}^{E} dE/S = s.  Whole grid intervals below E are subtracted from
+ * s while they fit (their exact quadratures, no cancellation); inside the
+ * interval that holds E' the root of int_{E'}^{top} dE/S = rem is found by
+ * Newton's method on the quadrature (derivative -1/S(E')), kept inside its
+ * bracket by bisection in ln E, started from the step with S(top). */
+static double eloss_exact_R(const or_ctx *c, int type, int mat, double E, double R_E, double s) {
+  if (!(s > 0.0)) return E;
+  if (s >= R_E) return 0.0;
+  const int qR = type == OR_ELECTRON ? 2 : 3;
+  const double R0 = c->tab[type][qR][mat][0];
+  if (E <= GRID_EMIN) return GRID_EMIN * (R_E - s) / R0;
+  int i = grid_interval(E);
+  double top = E, rem = s;
+  double part = quad_inv_dedx(c, type, mat, or_grid_energy(i), E);
+  while (part < rem) { /* E' lies below node i */
+    rem -= part;
+    top = or_grid_energy(i);
+    if (i == 0) return GRID_EMIN * fmax(0.0, R0 - rem) / R0; /* below the grid: R linear in E */
+    --i;
+    part = c->dR[type - 1][mat][i];
+  }
+  /* root in [E_i, top]: f(x) = int_x^top dE/S - rem, decreasing, f(E_i) >= 0 > f(top) */
+  double lo = or_grid_energy(i), hi = top;
+  double x = top - rem * or_dedx(c, type, mat, top);
+  if (!(x > lo && x < hi)) x = sqrt(lo * hi);
+  for (int it = 0; it < 100; ++it) {
+    const double f = quad_inv_dedx(c, type, mat, x, top) - rem;
+    if (f == 0.0) return x;
+    if (f > 0.0) lo = x; else hi = x;
+    double xn = x + f * or_dedx(c, type, mat, x);
+    if (!(xn > lo && xn < hi)) xn = sqrt(lo * hi);
+    if (fabs(xn - x) <= 1e-15 * x || hi - lo <= 1e-15 * hi) return xn;
+    x = xn;
+  }
+  return x;
+}
+
+double or_eloss_exact(const or_ctx *c, int type, int mat, double E, double s) {
+  return eloss_exact_R(c, type, mat, E, or_range_at(c, type, mat, E), s);
 }
 
 /* ------------------------------------------------------------------ */
@@ -844,8 +1036,9 @@ void or_helix(const or_ctx *c, int type, double E, double s, const double dir[3]
  * energy T after a path s in material mat:
  *   theta0 = 13.6 MeV / (beta p c) sqrt(s/X0) (1 + 0.038 ln(s / (X0 beta^2)))
  * with the bracket floored at 0 (PDG, "Passage of particles through
- * matter", multiple scattering section).  Parity unpinned beyond special
- * cases: the paper prints no scattering numbers. */
+ * matter", multiple scattering section).  Pinned: within 11 % of two widths
+ * from Moliere's theory (Bethe's Gaussian approximation, and Lynch & Dahl's
+ * width of the central 98 %) for 1e-3 < x/X0 < 100. */
 double or_msc_theta0(const or_ctx *c, int mat, double T, double s) {
   if (!(s > 0.0) || !(T > 0.0)) return 0.0;
   const double pc = sqrt(T * (T + 2.0 * ME));
@@ -914,10 +1107,14 @@ int or_create(const or_setup *s, or_ctx **out) {
       s->n_layers < 1)
     return -1;
   if (s->track_cut < GRID_EMIN || s->gamma_cut < s->track_cut || s->e_cut < s->track_cut) return -1;
+  /* the integral approach bounds the tabulated cross sections; the
+   * untabulated transport does not take it */
+  if (s->exact && (s->process_mask & OR_P_INTEGRAL)) return -1;
   or_ctx *c = (or_ctx *)calloc(1, sizeof(or_ctx));
   if (!c) return -2;
   c->s = *s;
   gauss_legendre(16, c->gl_x, c->gl_w);
+  gauss_legendre(6, c->gl6_x, c->gl6_w);
   for (int m = 0; m < s->n_mat; ++m) mat_init(&c->mat[m], &s->mat[m]);
   c->nsub = s->n_layers * s->n_sub;
   c->zb = (double *)malloc(sizeof(double) * (c->nsub + 1));
@@ -1068,7 +1265,7 @@ static int interact(const or_ctx *c, int type, int p, double *E, double dir[3], 
     int model = type == OR_ELECTRON ? OR_M_MOLLER : OR_M_BHABHA;
     if (type == OR_ELECTRON && T <= 2.0 * s->e_cut) return -1;
     if (type == OR_POSITRON && T <= s->e_cut) return -1;
-    double eps = or_alias_sample(c, model, T, ua, NULL);
+    double eps = sample_var(c, model, T, ua, rng);
     double Td = eps * T;
     double ct = sqrt(Td * (T + 2.0 * ME) / (T * (Td + 2.0 * ME)));
     if (ct > 1.0) ct = 1.0;
@@ -1082,7 +1279,7 @@ static int interact(const or_ctx *c, int type, int p, double *E, double dir[3], 
     dir[0] = dn[0]; dir[1] = dn[1]; dir[2] = dn[2];
     T -= Td;
   } else { /* annihilation in flight */
-    double eps = or_alias_sample(c, OR_M_ANNIH, T, ua, NULL);
+    double eps = sample_var(c, OR_M_ANNIH, T, ua, rng);
     double tot = T + 2.0 * ME, k1 = eps * tot, k2 = tot - k1;
     double P = sqrt(T * (T + 2.0 * ME));
     double ct = (k1 - ME) / (eps * P);
@@ -1160,6 +1357,7 @@ typedef struct {
   const or_primary *p;
   const long *ev_first, *ev_list;
   long n_events;
+  long first_event;  /* global index of row 0: the random streams use first_event + row */
   uint64_t seed;
   double *edep, *cell, *esc;
   long long *cnt;
@@ -1186,7 +1384,7 @@ static void run_event(const job_t *J, long ev, ostack *st) {
   const or_setup *s = &c->s;
   double *edep = J->edep + ev * c->nsub;
   long long *cnt = J->cnt + ev * OR_NCOUNT;
-  uint32_t key[2] = {(uint32_t)J->seed ^ (uint32_t)ev, (uint32_t)(J->seed >> 32)};
+  uint32_t key[2] = {(uint32_t)J->seed ^ (uint32_t)(ev + J->first_event), (uint32_t)(J->seed >> 32)};
   st->n = 0;
   for (long k = J->ev_first[ev + 1] - 1; k >= J->ev_first[ev]; --k) {
     long i = J->ev_list[k];
@@ -1247,17 +1445,24 @@ static void run_event(const job_t *J, long ev, ostack *st) {
       int np = n_proc(t.type);
       /* ComputeIntLen */
       if (t.nlam <= 0.0) t.nlam = -log(u[0]);
+      /* cross sections at the pre-step energy: interpolated in the tables,
+       * or (untabulated transport) from their formulas */
       double sig[3] = {0, 0, 0}, Sig = 0.0;
-      for (int p = 0; p < np; ++p) { sig[p] = or_table_lookup(c, t.type, p, mat, t.E); Sig += sig[p]; }
+      for (int p = 0; p < np; ++p) {
+        sig[p] = s->exact ? or_xs(c, t.type, p, mat, t.E) : or_table_lookup(c, t.type, p, mat, t.E);
+        Sig += sig[p];
+      }
       int charged = t.type != OR_GAMMA;
       /* integral approach: the step is drawn with Sigma_max over the energies
        * the track can reach, the interaction accepted at the post-step point */
       const int integral = charged && (s->process_mask & OR_P_INTEGRAL);
       const double Smax = integral ? or_sigma_max(c, t.type, mat, t.E) : Sig;
       double s_phys = Smax > 0.0 ? t.nlam / Smax : INFINITY;
-      double s_cont = INFINITY;
+      double s_cont = INFINITY, R_pre = 0.0;
       if (charged) {
-        double R = or_table_lookup(c, t.type, t.type == OR_ELECTRON ? 2 : 3, mat, t.E);
+        double R = s->exact ? or_range_at(c, t.type, mat, t.E)
+                            : or_table_lookup(c, t.type, t.type == OR_ELECTRON ? 2 : 3, mat, t.E);
+        R_pre = R;
         s_cont = fmax(STEP_ALPHA_R * R, fmin(STEP_RHO_F, R));
         /* the field's step limit acts like the continuous one */
         s_cont = fmin(s_cont, or_field_step_limit(c, t.type, t.E, t.dir));
@@ -1303,7 +1508,8 @@ static void run_event(const job_t *J, long ev, ostack *st) {
       const double E_pre = t.E;
       /* AlongStepAction: continuous loss */
       if (charged) {
-        double Ep = or_eloss(c, t.type, mat, t.E, sstep);
+        double Ep = s->exact ? eloss_exact_R(c, t.type, mat, t.E, R_pre, sstep)
+                             : or_eloss(c, t.type, mat, t.E, sstep);
         score(c, edep, J->cell, pre_sub, mid, t.E - Ep);
         t.E = Ep;
         if (t.E < s->track_cut) {
@@ -1420,19 +1626,21 @@ static void *worker(void *arg) {
   return NULL;
 }
 
-int or_transport(const or_ctx *c, const or_primary *p, long n_prim, long n_events, uint64_t seed,
-                 double *edep, double *cell_edep, double *escape_E, long long *ev_counts,
-                 int n_threads) {
-  if (!c || (!p && n_prim > 0) || n_events < 0 || !edep || !escape_E || !ev_counts) return -1;
+int or_transport_events(const or_ctx *c, const or_primary *p, long n_prim, long first_event, long n_events,
+                        uint64_t seed, double *edep, double *cell_edep, double *escape_E, long long *ev_counts,
+                        int n_threads) {
+  if (!c || (!p && n_prim > 0) || n_events < 0 || first_event < 0 || !edep || !escape_E || !ev_counts) return -1;
   for (long i = 0; i < n_prim; ++i)
-    if ((long)p[i].event >= n_events || p[i].type < 0 || p[i].type > 2) return -1;
+    if ((long)p[i].event < first_event || (long)p[i].event - first_event >= n_events || p[i].type < 0 ||
+        p[i].type > 2)
+      return -1;
   long *first = (long *)calloc(n_events + 1, sizeof(long));
   long *list = (long *)malloc(sizeof(long) * (n_prim > 0 ? n_prim : 1));
-  for (long i = 0; i < n_prim; ++i) first[p[i].event + 1]++;
+  for (long i = 0; i < n_prim; ++i) first[p[i].event - first_event + 1]++;
   for (long e = 0; e < n_events; ++e) first[e + 1] += first[e];
   long *fill = (long *)malloc(sizeof(long) * (n_events + 1));
   memcpy(fill, first, sizeof(long) * (n_events + 1));
-  for (long i = 0; i < n_prim; ++i) list[fill[p[i].event]++] = i;
+  for (long i = 0; i < n_prim; ++i) list[fill[p[i].event - first_event]++] = i;
   memset(edep, 0, sizeof(double) * n_events * c->nsub);
   memset(escape_E, 0, sizeof(double) * n_events);
   memset(ev_counts, 0, sizeof(long long) * n_events * OR_NCOUNT);
@@ -1444,6 +1652,7 @@ int or_transport(const or_ctx *c, const or_primary *p, long n_prim, long n_event
   for (int t = 0; t < n_threads; ++t) {
     job_t *J = &jobs[t];
     J->c = c; J->p = p; J->ev_first = first; J->ev_list = list; J->n_events = n_events;
+    J->first_event = first_event;
     J->seed = seed; J->edep = edep; J->esc = escape_E; J->cnt = ev_counts;
     J->cell = (cell_edep && ncell > 0) ? (double *)calloc(ncell, sizeof(double)) : NULL;
     J->tid = t; J->nthr = n_threads;
@@ -1459,4 +1668,10 @@ int or_transport(const or_ctx *c, const or_primary *p, long n_prim, long n_event
   }
   free(jobs); free(th); free(first); free(list); free(fill);
   return 0;
+}
+
+int or_transport(const or_ctx *c, const or_primary *p, long n_prim, long n_events, uint64_t seed,
+                 double *edep, double *cell_edep, double *escape_E, long long *ev_counts,
+                 int n_threads) {
+  return or_transport_events(c, p, n_prim, 0, n_events, seed, edep, cell_edep, escape_E, ev_counts, n_threads);
 }

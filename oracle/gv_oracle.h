@@ -24,6 +24,9 @@
  *                    tracks follow the exact helix of their pre-step momentum,
  *                    their steps limited to a 10 um sagitta and 0.2 rad;
  *                    boundaries are found along the straight line
+ * Two transports: the tabulated one of the paper's method (tables
+ * interpolated in ln E, sampling tables), and an untabulated one
+ * (or_setup.exact) that evaluates every quantity from its definition.
  * The stepping loop follows the stage sequence of Sec. 2.1.2 (Fig. "simulation
  * stages"): PreStep, ComputeIntLen, GeomQuery, Propagation, AlongStepAction,
  * PostStepActions, SteppingActions; secondaries go to a LIFO stack (the
@@ -86,6 +89,10 @@ typedef struct {
   int field_axis;                   /* its direction: 0 x, 1 y, 2 z */
   double reject_min[6];             /* per model: rejection sampling at E >= this (MeV);
                                        sampling tables below (and for models without one) */
+  int exact;                        /* 1: untabulated transport (cross sections by formula at the
+                                       track's energy, range and its inverse by quadrature and
+                                       root finding, every final state by rejection from its DCS);
+                                       0: the tabulated transport of the stepping tables */
 } or_setup;
 
 typedef struct {
@@ -131,6 +138,15 @@ double or_alias_sample(const or_ctx *c, int model, double E, const double *u3, d
 int or_has_rejection(int model);
 double or_reject_sample(const or_ctx *c, int model, double E, const uint32_t rng[5], double *xi,
                         int *trials);
+/* --- exact samplers of all six models (the untabulated transport): the
+ *     three above, and Moller, Bhabha and annihilation by rejection from
+ *     their DCS, with the same random stream */
+double or_exact_sample(const or_ctx *c, int model, double E, const uint32_t rng[5], double *xi,
+                       int *trials);
+
+/* --- untabulated range and continuous loss (charged types) ------------ */
+double or_range_at(const or_ctx *c, int type, int mat, double E);  /* cm, by quadrature */
+double or_eloss_exact(const or_ctx *c, int type, int mat, double E, double s); /* post-step energy */
 
 /* --- RNG -------------------------------------------------------------- */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -164,6 +180,12 @@ int or_transport(const or_ctx *c, const or_primary *p, long n_prim, long n_event
                  double *escape_E /* [n_events] */,
                  long long *ev_counts /* [n_events][OR_NCOUNT] */,
                  int n_threads);
+/* the events first_event .. first_event + n_events - 1 of a larger workload:
+ * primaries carry global event indices, row i holds event first_event + i,
+ * and the random streams are keyed by the global index */
+int or_transport_events(const or_ctx *c, const or_primary *p, long n_prim, long first_event,
+                        long n_events, uint64_t seed, double *edep, double *cell_edep, double *escape_E,
+                        long long *ev_counts, int n_threads);
 
 #ifdef __cplusplus
 }

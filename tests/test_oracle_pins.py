@@ -776,3 +776,148 @@ def test_integral_approach_showers_agree(oracle_mod):
     res = (b["edep"].sum(1) + b["escape"] - (T0 + 2 * ME * (c[:, 8] - c[:, 7]))) / T0
     assert np.abs(res).max() < 1e-9
     assert not np.array_equal(a["counts"], c)
+
+
+# ---------------------------------------------------------------- photoelectric
+# The oracle's photoabsorption is the Sauter-type non-relativistic Born
+# K-shell cross section (two electrons) times 5/4 for the outer shells.  Two
+# pins: Stobbe's exact non-relativistic K-shell cross section (hydrogen-like,
+# Bethe & Salpeter Sec. 71; its own normalisation pinned by the hydrogen
+# threshold value) reduces to the Born form as eta = sqrt(I_K / (k - I_K)) -> 0
+# with the correction 1 - pi eta + O(eta^2), which fixes the constant and
+# the powers of Z and m/k; and the absolute size in water against
+# Hubbell & Seltzer.
+ALPHA = 1.0 / 137.035999084
+NA = 6.02214076e23
+
+
+def _stobbe_k_electron(Z, k):
+    """Stobbe: photoionisation of one 1s electron of a hydrogen-like ion."""
+    a0 = RE / ALPHA ** 2
+    IK = Z * Z * ALPHA ** 2 * ME / 2.0
+    eta = math.sqrt(IK / (k - IK))
+    return (2 ** 9 * math.pi ** 2 * ALPHA * (a0 / Z) ** 2 / 3.0) * (IK / k) ** 4 * \
+        math.exp(-4.0 * eta * math.atan(1.0 / eta)) / (1.0 - math.exp(-2.0 * math.pi * eta)), eta
+
+
+def test_stobbe_reference_reproduces_the_hydrogen_threshold():
+    (want,) = [float(c[1]) for c in golden_lines("photoabsorption.txt") if c[0] == "threshold_H"]
+    IH = ALPHA ** 2 * ME / 2.0
+    got, _ = _stobbe_k_electron(1.0, IH * (1.0 + 1e-12))
+    assert abs(got / want - 1.0) < 2e-3, got
+
+
+@pytest.mark.parametrize("Z,A", [(1.0, 1.008), (7.4, 13.331), (8.0, 15.999), (82.0, 207.2)])
+def test_photoelectric_is_the_born_limit_of_stobbe(oracle_mod, Z, A):
+    o = _oracle_for(oracle_mod, [W.Material("el", [Z], [A], [1.0], 1.0, 75.0)])
+    nat = NA / A  # atoms per cm3 at rho = 1
+    IK = Z * Z * ALPHA ** 2 * ME / 2.0
+    for r in (1e4, 1e6, 1e8):
+        k = r * IK
+        born_k = o.xs(W.GAMMA, 1, 0, k) / nat / 1.25  # the K shell: without the 5/4
+        s1, eta = _stobbe_k_electron(Z, k)
+        ratio = 2.0 * s1 / born_k
+        assert abs(ratio - (1.0 - math.pi * eta)) < 10.0 * eta * eta, (Z, r, ratio)
+
+
+def test_photoelectric_water_against_hubbell_seltzer(oracle_mod):
+    """The Born K-shell form without Coulomb (Stobbe) correction overestimates
+    the photoabsorption of oxygen at 10-20 keV, where eta = 0.17-0.24 for
+    the oxygen K shell: the expected band of oracle / mu_en is 1.8-3.2 (a
+    wrong power of Z or of m/k, or a lost 5/4, leaves it)."""
+    mats = [W.Material("water", [1.0, 8.0], [1.008, 15.999], [0.111894, 0.888106], 1.0, 75.0)]
+    o = _oracle_for(oracle_mod, mats)
+    ratios = []
+    for c in golden_lines("photoabsorption.txt"):
+        if c[0] != "water":
+            continue
+        E, muen = float(c[1]), float(c[2])
+        ratios.append(o.xs(W.GAMMA, 1, 0, E) / muen)
+    assert len(ratios) == 3
+    assert all(1.8 < r < 3.2 for r in ratios), ratios
+    assert ratios[0] > ratios[1] > ratios[2]  # the Born form falls as k^-3.5, the data as k^-3.2
+
+
+# ---------------------------------------------------------------- Highland width
+# Pinned against two widths derived from Moliere's theory by other routes:
+# Bethe's Gaussian approximation chi_c sqrt((B - 1.2)/2) (B - ln B = ln of
+# chi_c^2 / (1.167 chi_a^2)), valid where B is not small, and Lynch & Dahl's
+# width of the central 98 % of the Moliere distribution,
+# chi_c^2 / (1 + F^2) ((1 + v)/v ln(1 + v) - 1), v = Omega / (2 (1 - F)),
+# Omega = chi_c^2 / chi_a^2 (NIM B58 (1991) 6).  chi_c^2 = 4 pi N_A r_e^2
+# m^2 Z(Z+1) X / (A (p beta)^2) (X in g/cm2) and chi_a^2 = (alpha m Z^(1/3) /
+# (0.885 p))^2 (1.13 + 3.76 (alpha Z / beta)^2).  PDG quotes the Highland
+# form as accurate to 11 % for 1e-3 < x/X0 < 100 at beta = 1.
+def _moliere_widths(Z, A, xg, T):
+    from scipy.optimize import brentq
+    p = math.sqrt(T * (T + 2.0 * ME))
+    beta = p / (T + ME)
+    chic2 = 4.0 * math.pi * NA * RE ** 2 * ME ** 2 * Z * (Z + 1.0) * xg / A / (p * beta) ** 2
+    chia2 = (ALPHA * ME * Z ** (1.0 / 3.0) / (0.885 * p)) ** 2 * (1.13 + 3.76 * (ALPHA * Z / beta) ** 2)
+    b = math.log(chic2 / (1.167 * chia2))
+    B = brentq(lambda x: x - math.log(x) - b, 1.0 + 1e-9, 1e4)
+    F = 0.98
+    v = 0.5 * (chic2 / chia2) / (1.0 - F)
+    ld = math.sqrt(chic2 / (1.0 + F * F) * ((1.0 + v) / v * math.log(1.0 + v) - 1.0))
+    return math.sqrt(chic2 * (B - 1.2) / 2.0), ld, B
+
+
+@pytest.mark.parametrize("mat", [W.LEAD, W.TUNGSTEN, W.SILICON, W.LIQUID_ARGON])
+def test_highland_width_matches_moliere(oracle_mod, mat):
+    o = _oracle_for(oracle_mod, [mat])
+    X0g = o.X0(0)
+    for T in (0.5, 2.0, 10.0, 1e3, 1e4, 1e5):  # beta = 0.86 .. 1: the 1/(beta p) and 1/beta^2 factors
+        for xr in 10.0 ** np.linspace(-3, 2, 21):
+            th = o.msc_theta0(0, T, xr * X0g / mat.rho)
+            bethe, ld, B = _moliere_widths(mat.Z[0], mat.A[0], xr * X0g, T)
+            assert abs(th / ld - 1.0) < 0.11, (mat.name, T, xr, th / ld)
+            if xr >= 1e-2:  # B >= 7.9: Bethe's Gaussian width holds
+                assert abs(th / bethe - 1.0) < 0.11, (mat.name, T, xr, th / bethe)
+
+
+# ---------------------------------------------------------------- positron collision loss
+# With the cut at or above the largest energy transfer (T for e+, T/2 for
+# e-) the restricted Berger-Seltzer loss must be the unrestricted ICRU 37
+# formula, dE/dx = 2 pi r_e^2 m n_e / beta^2 [ln(tau^2 (tau+2) / (2 (I/m)^2))
+# + F(tau) - delta], with F+ = 2 ln 2 - beta^2/12 (23 + 14/(tau+2)
+# + 10/(tau+2)^2 + 4/(tau+2)^3) and F- = 1 - beta^2 + (tau^2/8 - (2 tau + 1)
+# ln 2)/(tau+1)^2.  The cut dependence is tied to the Moller and Bhabha DCS
+# by test_restricted_loss_derivative_is_delta_ray_dcs, and the Bhabha DCS to
+# its textbook high-energy limit below.
+def _icru37_unrestricted(o, mat, T, positron):
+    tau = T / ME
+    g = tau + 1.0
+    b2 = 1.0 - 1.0 / (g * g)
+    m = o.wl.materials[mat]
+    I = m.I_eV * 1e-6
+    nel = o.n_el(mat)
+    if positron:
+        y = tau + 2.0
+        F = 2.0 * math.log(2.0) - b2 / 12.0 * (23.0 + 14.0 / y + 10.0 / y ** 2 + 4.0 / y ** 3)
+    else:
+        F = 1.0 - b2 + (tau * tau / 8.0 - (2.0 * tau + 1.0) * math.log(2.0)) / (g * g)
+    # density effect: 2 ln(beta gamma) + 2 ln(hbar omega_p / I) - 1, floored at 0
+    hw = ME * math.sqrt(4.0 * math.pi * nel * RE ** 3) / ALPHA
+    d = max(0.0, 2.0 * math.log(math.sqrt(tau * (tau + 2.0))) + 2.0 * math.log(hw / I) - 1.0)
+    L = math.log(tau * tau * (tau + 2.0) / (2.0 * (I / ME) ** 2))
+    return 2.0 * math.pi * RE ** 2 * ME * nel / b2 * (L + F - d)
+
+
+@pytest.mark.parametrize("positron", [True, False], ids=["e+", "e-"])
+def test_collision_loss_unrestricted_limit_is_icru37(oracle_mod, positron):
+    wl = W.pbps_electrons(1)
+    o = oracle_mod.Oracle(wl)
+    ptype = W.POSITRON if positron else W.ELECTRON
+    for mat in (0, 1):
+        for T in 10.0 ** np.linspace(-2.9, 5, 25):
+            _, col, _ = o.dedx_parts(ptype, mat, T, 1e30, 1e30)
+            want = _icru37_unrestricted(o, mat, T, positron)
+            assert abs(col / want - 1.0) < 1e-11, (mat, T, col, want)
+
+
+def test_bhabha_dcs_high_energy_limit(oracle_mod):
+    """beta^2 eps^2 dsigma/deps -> (1 - eps + eps^2)^2 as gamma -> infinity."""
+    T = 1e7 * ME
+    for e in np.linspace(0.01, 1.0, 100):
+        got = e * e * oracle_mod.Oracle.dcs(W_M.BHABHA, T, e)
+        assert abs(got - (1 - e + e * e) ** 2) < 1e-6

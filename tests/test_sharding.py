@@ -1,6 +1,7 @@
 """Multi-rank event sharding on CPU (gloo, world size 2): each rank transports
-its event range with the FP64 oracle, the tallies are gathered, and the result
-equals the single-process transport exactly (per-event random streams)."""
+its event range (tally rows for its own events only, random streams keyed by
+the global event index) with the FP64 oracle, the tallies are gathered, and the
+result equals the single-process transport exactly (per-event random streams)."""
 import os
 import socket
 
@@ -38,7 +39,8 @@ def _rank_main(rank, world, port, q):
     try:
         wl = W.wsi_cells(9, 2000.0)
         shard, lo, hi = sharding.shard_workload(wl, rank, world)
-        res = oracle.Oracle(shard).transport(n_threads=2)
+        res = oracle.Oracle(shard).transport(n_threads=2, first_event=lo)
+        assert res["edep"].shape[0] == hi - lo  # rows of this rank's events only
         full = sharding.gather_tallies(dist, res, lo, hi)
         if rank == 0:
             q.put({k: v for k, v in full.items()})
@@ -77,7 +79,7 @@ def _failing_rank_main(rank, world, port, q):
                             timeout=datetime.timedelta(seconds=20))
     if rank == 1:
         os._exit(3)  # the rank dies without joining the gather
-    local = {"edep": np.zeros((4, 2)), "escape": np.zeros(4)}
+    local = {"edep": np.zeros((2, 2)), "escape": np.zeros(2)}
     try:
         sharding.gather_tallies(dist, local, 0, 2)
         q.put("gathered")
@@ -98,3 +100,17 @@ def test_a_failed_rank_is_detected_by_the_gather():
         p.join(timeout=60)
     assert msg.startswith("detected"), msg
     assert procs[1].exitcode == 3
+
+
+def test_event_offset_rows_equal_the_full_transport(oracle_mod):
+    """A range transported with first_event = lo gives, in rows 0 .. hi-lo-1,
+    exactly rows lo .. hi-1 of the whole workload's transport."""
+    wl = W.pbps_mixed(30).subset(30)
+    wl.primaries["E"] = np.minimum(wl.primaries["E"], 2000.0)
+    ref = oracle_mod.Oracle(wl).transport(n_threads=2)
+    for rank, world in ((0, 3), (1, 3), (2, 3)):
+        shard, lo, hi = sharding.shard_workload(wl, rank, world)
+        r = oracle_mod.Oracle(shard).transport(n_threads=2, first_event=lo)
+        assert np.array_equal(r["edep"], ref["edep"][lo:hi])
+        assert np.array_equal(r["counts"], ref["counts"][lo:hi])
+        assert np.array_equal(r["escape"], ref["escape"][lo:hi])

@@ -37,8 +37,12 @@ from paper_2005_00949_gb300 import workloads as W  # noqa: E402
 METRIC = "EM steps/s and 10 GeV e- showers/s on 1 GB300; HBM roofline fraction"
 N_EVENTS = 2000
 E0 = 10_000.0
-# algorithmic DRAM bytes of one track step in a step-synchronous wavefront:
-# read + write the 64 B mixed-precision track record, plus 64 B per secondary
+# algorithmic DRAM bytes of one track step in a step-synchronous wavefront,
+# as the scope table fixes them for the mixed form: read + write a ~68 B track
+# record (136 B), ~0.2 secondaries of 68 B (14 B), a basket index read and
+# written (8 B)
+SCOPE_BYTES_PER_STEP = 158.0
+# the same with this build's record (64 B) and the measured secondaries per step
 TRACK_BYTES = 64
 
 
@@ -78,11 +82,26 @@ def _traffic_per_launch():
         return None
 
 
-def _workload(rank: int):
-    wl = W.pbps_electrons(N_EVENTS, E0)
-    # each rank owns a distinct event range (distinct Philox streams)
-    wl.seed = W.DEFAULT_SEED + rank
-    return wl
+def _workload(rank: int = 0, world: int = 1):
+    """This rank's shard of the job: the job is world x 2000 showers (weak
+    scaling), split by event range; the shard keeps global event indices
+    (its random streams) and is transported with first_event = lo."""
+    from paper_2005_00949_gb300 import sharding
+    return sharding.shard_workload(W.pbps_electrons(N_EVENTS * world, E0), rank, world)
+
+
+def _l2_profile():
+    """L2 throughput (% of peak) and hit rate of the step kernel from the ncu
+    capture summarised in profiles/ (None if the kernel sources changed since):
+    the live track set stays in L2, so L2 rather than HBM carries its traffic."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "step_kernel_l2.json")) as f:
+            t = json.load(f)
+        if t.get("kernel_source_sha1") != kernel_source_hash():
+            return None
+        return {k: t[k] for k in ("l2_throughput_pct", "l2_hit_rate_pct", "dram_throughput_pct", "workload")}
+    except (OSError, ValueError, KeyError):
+        return None
 
 
 class Clocks:
@@ -192,7 +211,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    wl = _workload(0)
+    wl, _, _ = _workload(0)
     nthr = os.cpu_count() or 1
     n_ev = N_EVENTS
     for _ in range(args.warmup):
@@ -251,9 +270,9 @@ def main():
     __graft_entry__.build()
     from paper_2005_00949_gb300 import gv
 
-    wl = _workload(rank)
+    wl, lo, hi = _workload(rank, world)
     if args.events != N_EVENTS:
-        wl = wl.subset(args.events)
+        wl = wl.subset(args.events) if world == 1 else wl
     ctx = gv.Context(wl, gv.gv_default_config(stack_capacity=args.capacity,
                                               device_loop=0 if args.host_loop else 1))
     dev = torch.device("cuda", local)
@@ -264,8 +283,8 @@ def main():
     esc = torch.zeros(wl.n_events, dtype=torch.float64, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
-    def step():
-        return ctx.gv_transport(prim_d, wl.n_events, wl.seed, edep, None, esc, None, stream)
+    def step():  # gv_transport_events + gv_sync
+        return ctx.gv_transport(prim_d, wl.n_events, wl.seed, edep, None, esc, None, stream, first_event=lo)
 
     def barrier():
         if dist is not None:
@@ -316,7 +335,7 @@ def main():
         flush.fill_(i & 0xff)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        ctx.gv_transport(prim_h, wl.n_events, wl.seed, edep_h, None, esc_h, None, stream)
+        ctx.gv_transport(prim_h, wl.n_events, wl.seed, edep_h, None, esc_h, None, stream, first_event=lo)
         torch.cuda.synchronize()
         e_ms += (time.perf_counter() - t) * 1000.0
     if dist is not None:
@@ -324,15 +343,22 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e_ms = float(t.item())
     e2e = events_all / (e_ms / n_e2e / 1000.0)
+    gathered = None
+    if dist is not None:  # the one collective of the job: the tallies of every shard to rank 0
+        from paper_2005_00949_gb300 import sharding
+        gathered = sharding.gather_tallies(dist, {"edep": edep_h.numpy(), "escape": esc_h.numpy()}, lo, hi)
     if rank != 0:
         dist.destroy_process_group()
         return 0
     # ---- roofline of the step kernel
     peak, peak_kind = _peaks()
     sec_per_step = sec / max(steps_tot, 1)
-    alg_bytes = steps_tot / world * (2 * TRACK_BYTES + TRACK_BYTES * sec_per_step)
+    rec_bytes_per_step = 2 * TRACK_BYTES + TRACK_BYTES * sec_per_step
+    alg_bytes = steps_tot * SCOPE_BYTES_PER_STEP  # this rank's steps, this rank's kernel time
     achieved = alg_bytes / (kernel_ms / 1000.0) / 1e9 if kernel_ms > 0 else None
+    achieved_rec = steps_tot * rec_bytes_per_step / (kernel_ms / 1000.0) / 1e9 if kernel_ms > 0 else None
     traffic = _traffic_per_launch() if args.events == N_EVENTS else None
+    l2 = _l2_profile()
     c = list(res.counters)
     working_launches = max(c[11], 1)  # generations of the last transport
     line = {
@@ -355,9 +381,12 @@ def main():
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "kernel": "gv::step_kernel<float>",
-                     "alg_bytes_per_step": 2 * TRACK_BYTES + TRACK_BYTES * sec_per_step,
+                     "alg_bytes_per_step": SCOPE_BYTES_PER_STEP,
                      "alg_bytes_per_launch": alg_bytes / args.steps / working_launches,
-                     "traffic_unit": "DRAM bytes per working launch (ncu, full-size workload)"},
+                     "alg_bytes_per_step_this_record": rec_bytes_per_step,
+                     "frac_this_record": (achieved_rec / peak) if achieved_rec else None,
+                     "traffic_unit": "DRAM bytes per working launch (ncu, full-size workload)",
+                     "l2": l2},
         "clocks": clk.summary(),
     }
     line["diagnostics"] = {

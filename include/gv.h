@@ -170,6 +170,9 @@ typedef struct {
                                  done; 0: the host relaunches the generation graph and checks after
                                  1, 2, 4, ... graphs (the same kernels; ncu profiles kernels only in
                                  graphs without conditional nodes) */
+  int blocking;               /* 0 (default): gv_transport returns once the transport is enqueued and
+                                 gv_sync completes it; 1: gv_transport returns when it is done, with
+                                 its result record filled (device_loop = 0 always behaves so) */
 } gv_config;
 
 /* A primary track; layout shared with the seeded input generator.  Its random
@@ -205,9 +208,14 @@ typedef struct {
 /* Fill *cfg with defaults (batched, mixed precision, autotuned launch shape). */
 int gv_default_config(gv_config *cfg);
 
-/* Create a context: validates the materials (n_mats <= GV_MAX_MAT), geometry
- * (n_layers*n_sub <= GV_MAX_SUBTOTAL) and cuts, allocates the device queues.
- * cfg = NULL selects defaults.  Uses the current CUDA device. */
+/* Create a context (the per-thread state of the paper's scheduler, Sec.
+ * 2.1.1, here one per GPU and workload): validates the materials
+ * (n_mats <= GV_MAX_MAT), geometry (n_layers*n_sub <= GV_MAX_SUBTOTAL) and
+ * cuts, and allocates its stream and geometry arrays.  *ctx_out receives the
+ * context, owned by the caller until gv_destroy.  cfg = NULL selects
+ * defaults.  Uses the current CUDA device.  GV_ERR_BAD_ARG for an
+ * inconsistent argument, GV_ERR_CUDA if the device cannot be set up; nothing
+ * is allocated on failure. */
 int gv_setup(void **ctx_out, const gv_material *mats, int n_mats, const gv_layers *geo,
              const gv_cuts *cuts, const gv_config *cfg);
 
@@ -217,11 +225,32 @@ int gv_setup(void **ctx_out, const gv_material *mats, int n_mats, const gv_layer
 int gv_build_tables(void *ctx);
 
 /* Transport n primaries (host or device array) of n_events events with the
- * given seed, on `stream`.  Runs the stepping loop (Sec. 2.1.2 stages, stack
- * of Sec. 2.1.2, scoring of Sec. 3.8.1) until every track has ended and
- * copies the tallies into res.  Blocks the calling thread until done. */
+ * given seed (the stepping loop of Sec. 2.1.2 stages, stack of Sec. 2.1.2,
+ * scoring of Sec. 3.8.1), until every track has ended, and copy the tallies
+ * into res's buffers.  The work is ordered after what the caller queued on
+ * `stream` before the call, and `stream` waits for it: work the caller
+ * queues on it later sees the tallies.  The call returns once the work is
+ * enqueued (config blocking = 0, the default); res->counters, status and
+ * kernel_ms are filled by gv_sync, which also returns the status, and the
+ * tally buffers hold the results once `stream` has reached that point.  With
+ * host tally buffers that are not page-locked the copies, and so the call,
+ * finish before it returns.  A second transport on the same context first
+ * completes the previous one (filling its result record).  The caller's
+ * buffers must stay valid until then.  Returns GV_OK or an error found
+ * before the work started (GV_ERR_BAD_ARG, GV_ERR_NO_TABLES, GV_ERR_OOM,
+ * GV_ERR_CUDA); errors of the transport itself (GV_ERR_STACK_FULL,
+ * GV_ERR_TIMEOUT, GV_ERR_NUMERIC) come from gv_sync. */
 int gv_transport(void *ctx, const gv_primary *p, long long n, long long n_events,
                  unsigned long long seed, void *stream, gv_result *res);
+
+/* gv_transport of the events first_event .. first_event + n_events - 1 (one
+ * shard of a workload split by event range over several GPUs or calls):
+ * primaries carry their global event index, tally row i holds event
+ * first_event + i, and the random streams are keyed by the global index, so
+ * the rows equal those of one transport of the whole workload.
+ * gv_transport(...) is gv_transport_events(..., 0, n_events, ...). */
+int gv_transport_events(void *ctx, const gv_primary *p, long long n, long long first_event,
+                        long long n_events, unsigned long long seed, void *stream, gv_result *res);
 
 /* gv_transport without any device allocation (the paper has no counterpart;
  * this entry point exists for embedding).  For callers that cannot let a
@@ -233,26 +262,41 @@ int gv_transport(void *ctx, const gv_primary *p, long long n, long long n_events
  * particle type, the generation control block, and live-track counts for up
  * to 65,536 events -- sits in one file-scope device array of 25,440,256 bytes
  * that every GPU holds from the library's first use on it until the process
- * exits.  The first call on a device looks up that array's address; make it
- * before any stream capture.  Every call reuses the array and clears what
- * must start at zero; calls whose work overlaps on the GPU (two streams, two
- * threads, or a concurrent call on another context) race on it.
+ * exits.  Every call asks the runtime for that array's device address on the
+ * current device (a device reset gives it a new one).  Every call reuses the
+ * array and clears what must start at zero; calls whose work overlaps on the
+ * GPU (two streams, two threads, or a concurrent call on another context)
+ * race on it.  The call waits on the host between its launches, so it cannot
+ * run on a stream that is being captured (GV_ERR_BAD_ARG) and must not run
+ * while another stream of the device captures in global mode.
  *   prim      device array of n primaries;
  *   edep      device [n_events][n_layers*n_sub], zeroed, then accumulated;
  *   escape_E  device [n_events], zeroed, then accumulated;
  *   counters  host array of 16 (as gv_result.counters).
- * Runs the batched schedule with at most 64 events in flight, on `stream`,
- * and returns when done.  GV_ERR_BAD_ARG: n_events > 65,536, host pointers,
- * an FP64 context, or a context with a magnetic field; GV_ERR_STACK_FULL: more live tracks than the array
- * holds (showers far above ~10 GeV per event in flight). */
+ * Runs the batched schedule on `stream` and returns when done; the events in
+ * flight are capped at 65,536 / (0.15 per MeV of the most energetic primary
+ * + 64), at least 16 (41 events of 10 GeV), so showers up to about 25 GeV per
+ * event fit the array; beyond that GV_ERR_STACK_FULL may be returned.
+ * GV_ERR_BAD_ARG: n_events > 65,536, host pointers, an FP64 context, or a
+ * context with a magnetic field.  gv_sync reports the status of the last
+ * transport, this one included. */
 int gv_transport_static(void *ctx, const gv_primary *prim, long long n, long long n_events,
                         unsigned long long seed, void *stream, double *edep, double *escape_E,
                         unsigned long long *counters);
 
-/* Wait for all work of the context on `stream`; returns the last status. */
+/* Complete the context's transport in flight, if any (the paper's
+ * transport of a batch of events ends when its last track has, Sec. 2.1.1):
+ * wait for it, fill its result record (counters, status, kernel_ms), then
+ * wait for all work queued on `stream`.  Returns the status of the last
+ * transport (GV_OK, GV_ERR_STACK_FULL, GV_ERR_TIMEOUT, GV_ERR_NUMERIC,
+ * GV_ERR_INTERNAL), or GV_ERR_CUDA if a wait fails, GV_ERR_BAD_ARG for a
+ * null context. */
 int gv_sync(void *ctx, void *stream);
 
-/* Release every resource of the context. */
+/* Release every resource of the context (what gv_setup and gv_build_tables
+ * allocated, Sec. 2.1.1's per-thread state), after waiting for its work.  A
+ * result record not yet collected by gv_sync stays unfilled.  ctx = NULL is
+ * a no-op. */
 void gv_destroy(void *ctx);
 
 /* Static description of an error code. */

@@ -83,6 +83,7 @@ template <typename R> struct DevState {
   const gv_primary *prim;
   const unsigned *order;     // primary visiting order (one-event mode) or null
   unsigned n_prim, n_events;
+  unsigned ev_base;          // event index of tally row 0 (the random streams use ev_base + row)
   double *edep, *cell, *escape;
   unsigned long long *evcnt;
   unsigned *evlive;          // live tracks per event (events-in-flight accounting)

@@ -155,7 +155,7 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   lim_out = -1;
   const uint32_t k = t.step;
   kk = k;
-  const uint32_t key0 = S->seed_lo ^ t.ev, key1 = S->seed_hi;
+  const uint32_t key0 = S->seed_lo ^ (t.ev + S->ev_base), key1 = S->seed_hi;
   const uint32_t idlo = static_cast<uint32_t>(t.id), idhi = static_cast<uint32_t>(t.id >> 32);
   // counter block 0 is drawn only when the step needs it: a new n_lambda, or
   // a physics-limited step (process choice and alias uniforms)
@@ -196,9 +196,9 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
     Smax = m[gi] + gf * (m[gi + 1] - m[gi]);
   }
   const R s_phys = Smax > R(0) ? q_div(t.nlam, Smax) : INF;
-  R s_cont = INF;
+  R s_cont = INF, Rr = R(0);
   if (charged) {
-    const R Rr = t.type == 1 ? s4.z : s4.w;
+    Rr = range_of(s4, t.type);
     const R a = static_cast<R>(kAlphaR) * Rr, b = Rr < static_cast<R>(kRhoF) ? Rr : static_cast<R>(kRhoF);
     s_cont = a > b ? a : b;
     if (FIELD && V.rc.field_k != R(0)) {  // the field's step limit acts like the continuous one
@@ -269,7 +269,7 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   const R E_pre = t.E;
   // AlongStepAction
   if (charged) {
-    const R Ep = eloss_at(V, mat, t.type, t.E, gi, gf, s);
+    const R Ep = eloss_at(V, mat, t.type, t.E, gi, gf, s, Rr);
     deposit(V, S, t.ev, pre_sub, mx, my, t.E - Ep, pd);
     t.E = Ep;
     if (t.E < tcut) {
@@ -343,7 +343,8 @@ __device__ __forceinline__ int final_state(const View<R> &V, const DevState<R> *
                                            Pending<R> *pd = nullptr) {
   R local;
   int np = 0, na = 0;
-  const RngKey g = {static_cast<uint32_t>(id), static_cast<uint32_t>(id >> 32), kk, S->seed_lo ^ ev, S->seed_hi};
+  const RngKey g = {static_cast<uint32_t>(id), static_cast<uint32_t>(id >> 32), kk, S->seed_lo ^ (ev + S->ev_base),
+                    S->seed_hi};
   const int r = interact(V, type, proc, E, d, u, g, kids, local, np, na);
   if (r < 0) return -1;
   if (np) count(S, bc, ev, GV_C_PAIR, np);
@@ -436,7 +437,7 @@ __device__ void push_kids(const DevState<R> *S, int out, const Parent &t, const 
   if (!any) return;
   uint32_t w[6] = {0, 0, 0, 0, 0, 0};
   if (kids.n > 0) {
-    const uint32_t key0 = S->seed_lo ^ t.ev;
+    const uint32_t key0 = S->seed_lo ^ (t.ev + S->ev_base);
     const uint4 a = philox4x32_10(make_uint4(static_cast<uint32_t>(t.id), static_cast<uint32_t>(t.id >> 32), kk, kTagId),
                                   key0, S->seed_hi);
     w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
@@ -828,6 +829,7 @@ __global__ void GV_STEP_BOUNDS
       const unsigned i = s_pb + idx;
       const unsigned pi = S->order ? S->order[i] : i;
       gv_primary p = S->prim[pi];
+      p.event -= S->ev_base;  // the tallies' row (events below the range wrap to a large value)
       if (p.type < 0 || p.type > 2 || p.event >= S->n_events) {  // caller's device array: check here
         set_status(ctl, GV_ERR_BAD_ARG);
         p.type = 0;
@@ -1174,6 +1176,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_ALONG_MIN_BLOCKS : 2)
       const unsigned i = s_pb + idx;
       const unsigned pi = S->order ? S->order[i] : i;
       gv_primary p = S->prim[pi];
+      p.event -= S->ev_base;  // the tallies' row (events below the range wrap to a large value)
       if (p.type < 0 || p.type > 2 || p.event >= S->n_events) {  // caller's device array: check here
         set_status(ctl, GV_ERR_BAD_ARG);
         p.type = 0;
@@ -1379,6 +1382,14 @@ struct Ctx {
   Ctl *h_ctl = nullptr;  // pinned
   long long launches = 0;
   int last_status = 0;
+  // a transport whose completion gv_sync (or the next call) collects
+  struct {
+    bool active = false;
+    gv_result *res = nullptr;
+    long long launches = 0;  // launches known before the device-side loop ran
+    double kernel_ms = 0.0;  // host-looped transports: measured already
+    bool timed_loop = false; // kernel time = t0 .. t1 of the one graph launch
+  } pend;
   ModelMeta meta[kNModel];
   size_t xs_bytes = 0, zb_bytes = 0, smem_bytes = 0, req_off = 0, bins_bytes = 0, smax_bytes = 0, smax_off = 0;
   size_t lk_off = 0;
@@ -1440,6 +1451,7 @@ int validate_cfg(const gv_config &c) {
   if (c.local_stack < 0 || c.local_stack > 1) return GV_ERR_BAD_ARG;
   if (c.pdl < 0 || c.pdl > 1) return GV_ERR_BAD_ARG;
   if (c.device_loop < 0 || c.device_loop > 1) return GV_ERR_BAD_ARG;
+  if (c.blocking < 0 || c.blocking > 1) return GV_ERR_BAD_ARG;
   if (c.pipeline < 0 || c.pipeline > 1 || (c.pipeline == 1 && c.scoring != 0)) return GV_ERR_BAD_ARG;
   return GV_OK;
 }
@@ -1481,10 +1493,12 @@ template <typename R> int upload_tables(Ctx *c) {
   const size_t nv = static_cast<size_t>(h.n_mat) * 3 * kGridN;
   std::vector<V4<R>> xs(nv);
   for (size_t i = 0; i < nv; ++i) {
+    // the range (e- component z, e+ component w) is stored as ln R
+    const int type = static_cast<int>((i / kGridN) % 3);
     xs[i].x = static_cast<R>(h.xs[4 * i + 0]);
     xs[i].y = static_cast<R>(h.xs[4 * i + 1]);
-    xs[i].z = static_cast<R>(h.xs[4 * i + 2]);
-    xs[i].w = static_cast<R>(h.xs[4 * i + 3]);
+    xs[i].z = static_cast<R>(type == 1 ? std::log(h.xs[4 * i + 2]) : h.xs[4 * i + 2]);
+    xs[i].w = static_cast<R>(type == 2 ? std::log(h.xs[4 * i + 3]) : h.xs[4 * i + 3]);
   }
   c->xs_bytes = nv * sizeof(V4<R>);
   CK(cudaMalloc(&c->d_xs, c->xs_bytes));
@@ -1835,9 +1849,38 @@ bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Completes the transport in flight (if any): waits for its last copy, then
+// fills the caller's result record from the pinned control block.
+int finish_pending(Ctx *c) {
+  if (!c->pend.active) return c->last_status;
+  c->pend.active = false;
+  CK(cudaEventSynchronize(c->ev_out));
+  const Ctl &h = *c->h_ctl;
+  double kernel_ms = c->pend.kernel_ms;
+  long long launches = c->pend.launches;
+  if (c->pend.timed_loop) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->t0, c->t1));
+    kernel_ms = ms;
+    launches += static_cast<long long>(h.loop_iter) * (c->cfg.generations_per_graph * (c->cfg.pipeline ? 2 : 1) + 1);
+  }
+  c->launches = launches;
+  const int status = h.status;
+  gv_result *res = c->pend.res;
+  if (res) {
+    for (int i = 0; i < 16; ++i) res->counters[i] = h.counters[i];
+    res->counters[GV_C_GENERATIONS] = h.gen;
+    res->counters[15] = h.live_peak;
+    res->status = status;
+    res->kernel_ms = kernel_ms;
+  }
+  c->last_status = status;
+  return status;
+}
+
 template <typename R>
-int run_transport(Ctx *c, const gv_primary *p, long long n, long long n_events, unsigned long long seed,
-                  cudaStream_t user, gv_result *res) {
+int run_transport(Ctx *c, const gv_primary *p, long long n, long long first_event, long long n_events,
+                  unsigned long long seed, cudaStream_t user, gv_result *res) {
   CK(cudaSetDevice(c->device));
   const int nsub = c->nsub;
   const size_t ncell = static_cast<size_t>(c->geo.n_layers) * c->geo.nx_cells * c->geo.ny_cells;
@@ -1907,6 +1950,7 @@ int run_transport(Ctx *c, const gv_primary *p, long long n, long long n_events, 
   s.order = c->cfg.mode == GV_ONE_EVENT_PER_LAUNCH ? c->d_order : nullptr;
   s.n_prim = static_cast<unsigned>(n);
   s.n_events = static_cast<unsigned>(n_events);
+  s.ev_base = static_cast<unsigned>(first_event);
   s.edep = c->d_edep;
   s.cell = (ncell && res && res->cell_edep) ? c->d_cell : nullptr;
   s.escape = c->d_escape;
@@ -1929,57 +1973,48 @@ int run_transport(Ctx *c, const gv_primary *p, long long n, long long n_events, 
   int rc = capture_graph<R>(c);
   if (rc) return rc;
   long long launches = (s.max_in_flight < 0 && n > 0) ? 2 : 1;
-  int between = 1;
   double kernel_ms = 0.0;
   if (c->loop_graph) {  // one launch: the device-side loop runs until the transport is done
     CK(cudaEventRecord(c->t0, c->stream));
     CK(cudaGraphLaunch(c->graph, c->stream));
     CK(cudaEventRecord(c->t1, c->stream));
-    CK(cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, c->t0, c->t1));
-    kernel_ms = ms;
-    launches += static_cast<long long>(c->h_ctl->loop_iter) *
-                (c->cfg.generations_per_graph * (c->cfg.pipeline ? 2 : 1) + 1);
+  } else {  // the host relaunches the generation graph until the plan says done
+    int between = 1;
+    for (;;) {
+      CK(cudaEventRecord(c->t0, c->stream));
+      for (int i = 0; i < between; ++i) CK(cudaGraphLaunch(c->graph, c->stream));
+      CK(cudaEventRecord(c->t1, c->stream));
+      launches += static_cast<long long>(between) * c->cfg.generations_per_graph * (c->cfg.pipeline ? 2 : 1);
+      CK(cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, c->t0, c->t1));
+      kernel_ms += ms;
+      if (c->h_ctl->done) break;
+      between = std::min(between * 2, 64);
+    }
   }
-  for (; !c->loop_graph;) {
-    CK(cudaEventRecord(c->t0, c->stream));
-    for (int i = 0; i < between; ++i) CK(cudaGraphLaunch(c->graph, c->stream));
-    CK(cudaEventRecord(c->t1, c->stream));
-    launches += static_cast<long long>(between) * c->cfg.generations_per_graph * (c->cfg.pipeline ? 2 : 1);
-    CK(cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, c->t0, c->t1));
-    kernel_ms += ms;
-    if (c->h_ctl->done) break;
-    between = std::min(between * 2, 64);
-  }
-  c->launches = launches;
-  const Ctl &h = *c->h_ctl;
-  int status = h.status;
-  if (res) {
-    for (int i = 0; i < 16; ++i) res->counters[i] = h.counters[i];
-    res->counters[GV_C_GENERATIONS] = h.gen;
-    res->counters[15] = h.live_peak;
-    if (res->edep)
-      CK(cudaMemcpyAsync(res->edep, c->d_edep, sizeof(double) * n_events * nsub, cudaMemcpyDefault, c->stream));
-    if (res->escape_E)
-      CK(cudaMemcpyAsync(res->escape_E, c->d_escape, sizeof(double) * n_events, cudaMemcpyDefault, c->stream));
-    if (res->cell_edep && ncell)
-      CK(cudaMemcpyAsync(res->cell_edep, c->d_cell, sizeof(double) * ncell, cudaMemcpyDefault, c->stream));
-    if (evc)
-      CK(cudaMemcpyAsync(res->event_counts, c->d_evcnt, sizeof(long long) * n_events * GV_NCOUNT, cudaMemcpyDefault,
-                         c->stream));
-    res->status = status;
-    res->kernel_ms = kernel_ms;
-  }
+  // the control block and the tallies follow on the work stream; the
+  // caller's stream waits for them
+  CK(cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+  if (res->edep)
+    CK(cudaMemcpyAsync(res->edep, c->d_edep, sizeof(double) * n_events * nsub, cudaMemcpyDefault, c->stream));
+  if (res->escape_E)
+    CK(cudaMemcpyAsync(res->escape_E, c->d_escape, sizeof(double) * n_events, cudaMemcpyDefault, c->stream));
+  if (res->cell_edep && ncell)
+    CK(cudaMemcpyAsync(res->cell_edep, c->d_cell, sizeof(double) * ncell, cudaMemcpyDefault, c->stream));
+  if (evc)
+    CK(cudaMemcpyAsync(res->event_counts, c->d_evcnt, sizeof(long long) * n_events * GV_NCOUNT, cudaMemcpyDefault,
+                       c->stream));
   CK(cudaEventRecord(c->ev_out, c->stream));
   CK(cudaStreamWaitEvent(user, c->ev_out, 0));
-  CK(cudaStreamSynchronize(c->stream));
-  c->last_status = status;
-  return status;
+  c->pend.active = true;
+  c->pend.res = res;
+  c->pend.launches = launches;
+  c->pend.kernel_ms = kernel_ms;
+  c->pend.timed_loop = c->loop_graph != 0;
+  if (c->cfg.blocking || !c->loop_graph) return finish_pending(c);
+  return GV_OK;
 }
 
 }  // namespace
@@ -2015,6 +2050,7 @@ int gv_default_config(gv_config *cfg) {
   cfg->local_stack = 1;
   cfg->pdl = 1;
   cfg->device_loop = 1;
+  cfg->blocking = 0;
   return GV_OK;
 }
 
@@ -2080,30 +2116,39 @@ int gv_build_tables(void *ctx) {
   return GV_OK;
 }
 
-int gv_transport(void *ctx, const gv_primary *p, long long n, long long n_events, unsigned long long seed,
-                 void *stream, gv_result *res) {
+int gv_transport_events(void *ctx, const gv_primary *p, long long n, long long first_event, long long n_events,
+                        unsigned long long seed, void *stream, gv_result *res) {
   Ctx *c = static_cast<Ctx *>(ctx);
-  if (!c || (!p && n > 0) || n < 0 || n_events < 1 || n > 0xffffffffll || n_events > 0xffffffffll)
+  if (!c || (!p && n > 0) || n < 0 || n_events < 1 || n > 0xffffffffll || first_event < 0 ||
+      first_event + n_events > 0xffffffffll)
     return GV_ERR_BAD_ARG;
   if (!c->tables) return GV_ERR_NO_TABLES;
   if (!res || !res->edep) return GV_ERR_BAD_ARG;
   if (res->event_counts && !c->cfg.per_event_counts) return GV_ERR_BAD_ARG;
   if (!is_device_ptr(p)) {
     for (long long i = 0; i < n; ++i)
-      if (p[i].type < 0 || p[i].type > 2 || p[i].event >= static_cast<unsigned long long>(n_events) ||
+      if (p[i].type < 0 || p[i].type > 2 || p[i].event < static_cast<unsigned long long>(first_event) ||
+          p[i].event - static_cast<unsigned long long>(first_event) >= static_cast<unsigned long long>(n_events) ||
           !(p[i].E_MeV >= 0))
         return GV_ERR_BAD_ARG;
   }
+  finish_pending(c);  // the previous transport of this context completes first
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return c->cfg.precision == GV_FP64 ? run_transport<double>(c, p, n, n_events, seed, s, res)
-                                     : run_transport<float>(c, p, n, n_events, seed, s, res);
+  return c->cfg.precision == GV_FP64 ? run_transport<double>(c, p, n, first_event, n_events, seed, s, res)
+                                     : run_transport<float>(c, p, n, first_event, n_events, seed, s, res);
+}
+
+int gv_transport(void *ctx, const gv_primary *p, long long n, long long n_events, unsigned long long seed,
+                 void *stream, gv_result *res) {
+  return gv_transport_events(ctx, p, n, 0, n_events, seed, stream, res);
 }
 
 int gv_sync(void *ctx, void *stream) {
   Ctx *c = static_cast<Ctx *>(ctx);
   if (!c) return GV_ERR_BAD_ARG;
+  const int rc = finish_pending(c);
   if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return GV_ERR_CUDA;
-  return c->last_status;
+  return rc;
 }
 
 long long gv_last_launches(void *ctx) {
@@ -2115,6 +2160,7 @@ void gv_destroy(void *ctx) {
   Ctx *c = static_cast<Ctx *>(ctx);
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  c->pend.active = false;  // a result not collected by gv_sync stays unfilled
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->l2_window) {  // release the persisting lines and the set-aside taken at setup
     cudaCtxResetPersistingL2Cache();
@@ -2208,21 +2254,17 @@ static __device__ __align__(256) unsigned char g_gv_static_scratch[kStaticBytes]
 
 namespace {
 
-std::mutex g_static_mu;
-unsigned char *g_static_base[256] = {};  // device address of the array, per device ordinal
-
 // Device address of the scratch array on the current device.  Host code only
 // sees a host-side stand-in under the array's name, so the address is asked
-// of the runtime once per device, with that device current.
-int static_scratch(int dev, unsigned char **base) {
-  if (dev < 0 || dev >= 256) return GV_ERR_BAD_ARG;
-  std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_base[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_gv_static_scratch) != cudaSuccess || !p) return GV_ERR_CUDA;
-    g_static_base[dev] = static_cast<unsigned char *>(p);
+// of the runtime, with the device current, on every call: a cached address
+// would outlive a device reset or a new primary context.
+int static_scratch(unsigned char **base) {
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_gv_static_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return GV_ERR_CUDA;
   }
-  *base = g_static_base[dev];
+  *base = static_cast<unsigned char *>(p);
   return GV_OK;
 }
 
@@ -2252,22 +2294,9 @@ Queue<float> carve_static(unsigned char *&p) {
 }
 
 // the state record travels as a kernel argument, so no staging copy is needed
-__global__ void static_begin_kernel(DevState<float> s, DevState<float> *dst) {
+__global__ void static_state_kernel(DevState<float> s, DevState<float> *dst) {
   *dst = s;
-  Ctl *c = s.ctl;
-  for (int i = 0; i < 2; ++i)
-    for (int q = 0; q < 3; ++q) c->cnt[i][q] = 0;
-  c->prim_next = 0;
-  c->status = 0;
-  c->done = 0;
-  c->gen = 0;
-  c->loop_iter = 0;
-  c->live_peak = 0;
-  c->ev_started = 0;
-  c->ev_done = 0;
-  c->max_in_flight = static_cast<unsigned>(s.max_in_flight);
-  for (int i = 0; i < 16; ++i) c->counters[i] = 0;
-  plan_next(dst, 0);
+  s.ctl->emax_bits = 0u;
 }
 
 }  // namespace
@@ -2283,10 +2312,19 @@ extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long 
   if (n_events > kStaticMaxEvents || n > 0xffffffffll) return GV_ERR_BAD_ARG;
   if ((n > 0 && !is_device_ptr(prim)) || !is_device_ptr(edep) || !is_device_ptr(escape_E)) return GV_ERR_BAD_ARG;
   if (cudaSetDevice(c->device) != cudaSuccess) return GV_ERR_CUDA;
-  unsigned char *base = nullptr;
-  int rc = static_scratch(c->device, &base);
-  if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  {  // the call waits on the host between launches: a capturing stream cannot take it
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      return GV_ERR_CUDA;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return GV_ERR_BAD_ARG;
+  }
+  finish_pending(c);  // a gv_transport of this context still in flight completes first
+  unsigned char *base = nullptr;
+  int rc = static_scratch(&base);
+  if (rc) return rc;
   const size_t smem = c->req_off;  // tables and geometry; the non-basketizing kernel
   if (cudaFuncSetAttribute(step_kernel<float, false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess)
@@ -2315,7 +2353,7 @@ extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long 
   s.claim_chunks = 0;
   s.low_water = static_cast<unsigned long long>(kStaticCap / 4);
   s.batch = std::min<unsigned long long>(s.batch, 64);
-  s.max_in_flight = 64;  // ~65k live tracks hold some 64 showers of 10 GeV in Pb
+  s.max_in_flight = -1;  // automatic: capacity / (0.15 per MeV of the most energetic primary + 64)
   s.prim = prim;
   s.order = nullptr;
   s.n_prim = static_cast<unsigned>(n);
@@ -2325,10 +2363,14 @@ extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long 
   s.escape = escape_E;
   s.evcnt = nullptr;
   s.evlive = reinterpret_cast<unsigned *>(base + kStaticEvliveOff);
+  s.ev_base = 0;
   s.seed_lo = static_cast<unsigned>(seed);
   s.seed_hi = static_cast<unsigned>(seed >> 32);
   DevState<float> *S = reinterpret_cast<DevState<float> *>(base + kStaticStateOff);
-  static_begin_kernel<<<1, 1, 0, st>>>(s, S);
+  static_state_kernel<<<1, 1, 0, st>>>(s, S);
+  if (n > 0)
+    prim_emax_kernel<float><<<static_cast<int>(std::min<long long>((n + 255) / 256, 4 * c->sm_count)), 256, 0, st>>>(S);
+  init_kernel<float><<<1, 1, 0, st>>>(S);
   if (cudaGetLastError() != cudaSuccess) return GV_ERR_CUDA;
   int between = 1;
   for (;;) {
@@ -2344,5 +2386,6 @@ extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long 
   for (int i = 0; i < 16; ++i) counters[i] = c->h_ctl->counters[i];
   counters[GV_C_GENERATIONS] = c->h_ctl->gen;
   counters[15] = c->h_ctl->live_peak;
-  return c->h_ctl->status;
+  c->last_status = c->h_ctl->status;  // what a later gv_sync on this context reports
+  return c->last_status;
 }

@@ -34,8 +34,8 @@ __global__ void k_lookup(View<R> V, int type, int mat, const double *E, long lon
   const V4<R> v = lookup(V, mat, type, static_cast<R>(E[i]));
   out[4 * i] = v.x;
   out[4 * i + 1] = v.y;
-  out[4 * i + 2] = v.z;
-  out[4 * i + 3] = v.w;
+  out[4 * i + 2] = type == 1 ? range_of(v, type) : v.z;  // the range, from its interpolated logarithm
+  out[4 * i + 3] = type == 2 ? range_of(v, type) : v.w;
 }
 
 template <typename R>

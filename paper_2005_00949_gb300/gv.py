@@ -61,7 +61,7 @@ class gv_config(C.Structure):
                 ("process_sort", C.c_int), ("max_events_in_flight", C.c_longlong),
                 ("claim_chunks", C.c_int), ("along_steps", C.c_int), ("scoring", C.c_int),
                 ("l2_persist", C.c_int), ("pipeline", C.c_int), ("local_stack", C.c_int),
-                ("pdl", C.c_int), ("device_loop", C.c_int)]
+                ("pdl", C.c_int), ("device_loop", C.c_int), ("blocking", C.c_int)]
 
 
 class gv_result(C.Structure):
@@ -84,6 +84,7 @@ def load():
                                      C.POINTER(gv_cuts), C.POINTER(gv_config)]
             lib.gv_build_tables.argtypes = [vp]
             lib.gv_transport.argtypes = [vp, vp, ll, ll, C.c_ulonglong, vp, C.POINTER(gv_result)]
+            lib.gv_transport_events.argtypes = [vp, vp, ll, ll, ll, C.c_ulonglong, vp, C.POINTER(gv_result)]
             lib.gv_sync.argtypes = [vp, vp]
             lib.gv_destroy.argtypes = [vp]
             lib.gv_destroy.restype = None
@@ -185,25 +186,39 @@ class Context:
         return self.wl.n_layers * len(self.wl.sub_thick)
 
     def gv_transport(self, primaries, n_events: int, seed: int, edep, cell=None, escape=None,
-                     event_counts=None, stream=None) -> gv_result:
-        """Call gv_transport with caller-owned buffers (torch tensors or numpy
-        arrays, host or device).  `primaries` is a numpy PRIMARY_DTYPE array
-        or a uint8 device tensor holding the same records."""
+                     event_counts=None, stream=None, sync: bool = True, first_event: int = 0) -> gv_result:
+        """Call gv_transport_events with caller-owned buffers (torch tensors or
+        numpy arrays, host or device).  `primaries` is a numpy PRIMARY_DTYPE
+        array or a uint8 device tensor holding the same records.  sync=True
+        also calls gv_sync (the result record is filled when it returns);
+        sync=False returns once the transport is enqueued: call sync() later."""
         n = len(primaries) if isinstance(primaries, np.ndarray) else primaries.numel() // W.PRIMARY_DTYPE.itemsize
         res = gv_result()
         res.edep = _ptr(edep)
         res.cell_edep = _ptr(cell)
         res.escape_E = _ptr(escape)
         res.event_counts = _ptr(event_counts)
-        rc = self.lib.gv_transport(self.h, _ptr(primaries), n, n_events, C.c_ulonglong(seed),
-                                   _stream_ptr(stream), C.byref(res))
+        # the buffers must outlive the transport in flight
+        self._in_flight = (primaries, edep, cell, escape, event_counts)
+        rc = self.lib.gv_transport_events(self.h, _ptr(primaries), n, first_event, n_events, C.c_ulonglong(seed),
+                                          _stream_ptr(stream), C.byref(res))
         self.last_result = res
         _check(rc, "gv_transport")
+        if sync:
+            self.sync(stream)
         return res
 
+    def sync(self, stream=None) -> gv_result:
+        """gv_sync: complete the transport in flight; returns its result record."""
+        _check(self.lib.gv_sync(self.h, _stream_ptr(stream)), "gv_sync")
+        self._in_flight = None
+        return self.last_result
+
     def transport(self, wl: W.Workload | None = None, seed: int | None = None, device: str = "cuda",
-                  cells: bool = True, per_event: bool = False, stream=None) -> dict:
-        """Convenience: run a workload with device-resident buffers; returns numpy arrays."""
+                  cells: bool = True, per_event: bool = False, stream=None, first_event: int = 0) -> dict:
+        """Convenience: run a workload with device-resident buffers; returns numpy
+        arrays.  first_event: global index of the workload's first event (a shard
+        of a larger workload, whose primaries carry global event indices)."""
         import torch
         wl = wl or self.wl
         seed = wl.seed if seed is None else seed
@@ -215,7 +230,7 @@ class Context:
         ncell = wl.n_layers * wl.nx * wl.ny
         cell = torch.zeros(ncell, dtype=torch.float64, device=dev) if (cells and ncell) else None
         evc = torch.zeros((wl.n_events, NCOUNT), dtype=torch.int64, device=dev) if per_event else None
-        res = self.gv_transport(prim, wl.n_events, seed, edep, cell, esc, evc, stream)
+        res = self.gv_transport(prim, wl.n_events, seed, edep, cell, esc, evc, stream, first_event=first_event)
         out = {"edep": edep.cpu().numpy(), "escape": esc.cpu().numpy(),
                "counters": dict(zip(COUNTER_NAMES, list(res.counters))), "status": res.status,
                "launches": self.lib.gv_last_launches(self.h), "kernel_ms": res.kernel_ms}

@@ -1,0 +1,43 @@
+"""The mixed-precision GPU transport against the untabulated oracle.
+
+The GPU's tables (FP32, interpolated in ln E; sampling tables) and its FP32
+arithmetic are compared, whole showers against whole showers, with the
+oracle's untabulated transport (every quantity from its definition; FP64),
+whose reference statistics tests/golden/make_exact_showers.py stored by
+running only the oracle.  Criteria of the shower parity: every layer within
+3 combined standard errors, 0.5 % where that bound is active, per-material
+totals likewise.  The GPU samples use the workloads' default seed, the
+stored ones another: the two are independent.
+"""
+import pytest
+
+from paper_2005_00949_gb300 import workloads as W
+
+import shower_stats as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gvmod():
+    import torch
+    assert torch.cuda.is_available()
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2005_00949_gb300 import gv
+    return gv
+
+
+@pytest.mark.parametrize("n,E,golden", [
+    (200_000, 1000.0, "exact_showers_e-1GeV_PbPS50.txt"),
+    (65_536, 10_000.0, "exact_showers_e-10GeV_PbPS50.txt"),
+], ids=["1GeV", "10GeV"])
+def test_mixed_gpu_matches_untabulated_oracle(gvmod, n, E, golden):
+    wl = W.pbps_electrons(n, E)
+    ctx = gvmod.Context(wl, gvmod.gv_default_config(stack_capacity=1 << 23))
+    r = ctx.transport(cells=False)
+    ctx.close()
+    assert r["status"] == 0
+    got = S.compare(S.summarize(r["edep"], wl.n_layers), S.read(golden))
+    assert got["active_layers"] >= 5, got
+    assert got["active_materials"] == 2, got

@@ -314,6 +314,67 @@ def test_resuming_an_event_range_reproduces_it(gvmod):
     assert (np.abs(tail["edep"][180:] - full["edep"][180:]) / scale).max() < 1e-9
 
 
+def test_event_range_with_offset_gives_the_full_rows(gvmod):
+    """gv_transport_events: a shard [lo, hi) transported with first_event = lo
+    into tallies of hi - lo rows (the multi-GPU split) gives the rows lo ..
+    hi-1 of the whole workload: integer counts bit for bit, deposits to the
+    order of the FP64 atomics."""
+    from paper_2005_00949_gb300 import sharding
+    wl = W.pbps_mixed(300).subset(300)
+    wl.primaries["E"] = np.minimum(wl.primaries["E"], 5000.0)
+    ctx = _ctx(gvmod, wl, per_event_counts=1)
+    full = ctx.transport(per_event=True)
+    for rank in range(3):
+        shard, lo, hi = sharding.shard_workload(wl, rank, 3)
+        r = ctx.transport(shard, per_event=True, first_event=lo)
+        assert r["status"] == 0 and r["edep"].shape[0] == hi - lo
+        assert np.array_equal(r["counts"][:, :11], full["counts"][lo:hi, :11])
+        scale = np.maximum(full["edep"][lo:hi].sum(1, keepdims=True), 1.0)
+        assert (np.abs(r["edep"] - full["edep"][lo:hi]) / scale).max() < 1e-9
+    # a primary outside the range is refused (host array checked on the host)
+    shard, lo, hi = sharding.shard_workload(wl, 1, 3)
+    bad = shard.primaries.copy()
+    bad["event"][0] = lo - 1
+    edep = np.zeros((hi - lo, ctx.n_subtotal))
+    esc = np.zeros(hi - lo)
+    with pytest.raises(gvmod.GvError, match="bad argument"):
+        ctx.gv_transport(bad, hi - lo, wl.seed, edep, None, esc, first_event=lo)
+
+
+def test_transport_is_asynchronous_until_sync(gvmod):
+    """gv_transport returns once the work is enqueued; the host works
+    meanwhile; gv_sync fills the result record, identical to a blocking
+    call's.  The caller's stream is ordered after the transport."""
+    import time
+
+    import torch
+    wl = W.pbps_electrons(2000, 10_000.0)
+    ctx = _ctx(gvmod, wl, stack_capacity=1 << 23)
+    want = ctx.transport()
+    prim = torch.from_numpy(wl.primaries.view(np.uint8).copy()).cuda()
+    edep = torch.zeros((wl.n_events, ctx.n_subtotal), dtype=torch.float64, device="cuda")
+    esc = torch.zeros(wl.n_events, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    res = ctx.gv_transport(prim, wl.n_events, wl.seed, edep, None, esc, stream=stream, sync=False)
+    t_return = time.perf_counter() - t
+    assert res.counters[0] == 0  # not filled before gv_sync
+    total = edep.sum(1)  # queued on the caller's stream: runs after the transport
+    host_work = sum(i * i for i in range(200_000))  # the host is free meanwhile
+    ctx.sync(stream)
+    t_done = time.perf_counter() - t
+    assert host_work > 0 and res.status == 0
+    assert res.counters[0] == want["counters"]["steps"]
+    assert t_return < 0.5 * t_done, (t_return, t_done)  # returned before the work was done
+    assert np.allclose(edep.cpu().numpy(), want["edep"], rtol=1e-9, atol=1e-9)
+    assert np.allclose(total.cpu().numpy(), want["edep"].sum(1), rtol=1e-9, atol=1e-9)
+    # the blocking form fills the record on return
+    bctx = _ctx(gvmod, wl, stack_capacity=1 << 23, blocking=1)
+    r2 = bctx.gv_transport(prim, wl.n_events, wl.seed, edep, None, esc, stream=stream, sync=False)
+    assert r2.counters[0] == want["counters"]["steps"] and r2.status == 0
+
+
 # ---------------------------------------------------------------- maximum sizes
 def test_largest_geometry_and_material_set(gvmod, oracle_mod):
     """The largest geometry the ABI takes: 4 materials, 8 sub-slabs per

@@ -175,8 +175,22 @@ CASES = [(0, 0, (1e-3, 1e5)), (0, 1, (1e-3, 10.0)), (0, 2, (1.03, 1e5)),
 PROC_MODEL = {(0, 0): 0, (0, 2): 1, (1, 0): 2, (2, 0): 2, (1, 1): 3, (2, 1): 4, (2, 2): 5}
 
 
+# energies whose FP32 value is a difference of larger terms carry an absolute
+# error of the parent's size: pair leptons (x k - m), the survivor of a
+# bremsstrahlung emission (T - k) and local deposits (sums of such terms);
+# every other energy is a product and is held relative to itself
+DIFF_SURVIVOR = {(1, 0), (2, 0)}
+
+
 @pytest.mark.parametrize("ptype,proc,rng_E", CASES)
 def test_interaction_matches_oracle(torch, ctx, oracle_pbps, ptype, proc, rng_E):
+    """Final states against the oracle's, given the same uniforms: the return
+    code, the number and types of the products exactly; every energy to tol
+    relative to itself (tol relative to the parent's energy where it is a
+    difference of larger terms); every direction (unit vector) to tol per
+    component.  Cases within 1e-5 of the 1 MeV e cut or the 1 keV tracking
+    cut (tracked or deposited depends on rounding) are set aside and their
+    fraction bounded, as are alias knife edges."""
     rng = np.random.default_rng(50 + 3 * ptype + proc)
     n = 4_099
     E = 10 ** rng.uniform(math.log10(rng_E[0]), math.log10(rng_E[1]), n)
@@ -192,33 +206,35 @@ def test_interaction_matches_oracle(torch, ctx, oracle_pbps, ptype, proc, rng_E)
     gret = ret.cpu().numpy()
     tol = TOL[ctx.prec]
     model = PROC_MODEL.get((ptype, proc))
-    skip = np.zeros(n, bool)
+    knife = np.zeros(n, bool)
     if model is not None:
-        skip |= _knife_edge_mask(oracle_pbps, model, E, u[:, 2:5])
+        knife |= _knife_edge_mask(oracle_pbps, model, E, u[:, 2:5])
+    cut_edge = np.zeros(n, bool)
     checked = 0
     for i in range(n):
         r, o = oracle_pbps.interact(ptype, proc, E[i], d[i], u[i])
-        # a Compton/photo/pair lepton at the e cut (1 MeV) is tracked or
-        # deposited on the spot depending on rounding
-        if ptype == 0 and (any(abs(o[7 + 5 * j] - 1.0) < 1e-5 for j in range(int(o[5]))) or
-                           abs(o[4] - 1.0) < 1e-5):
-            skip[i] = True
-        if skip[i]:
+        energies = [o[7 + 5 * j] for j in range(int(o[5]))] + ([o[0]] if r == 1 else []) + [o[4]]
+        if any(abs(e - 1.0) < 1e-5 or abs(e / 1e-3 - 1.0) < 1e-5 for e in energies):
+            cut_edge[i] = True
+        if knife[i] or cut_edge[i]:
             continue
         checked += 1
         g = got[i]
         assert gret[i] == r, (i, E[i], gret[i], r)
         assert int(g[5]) == int(o[5]), (i, E[i])
-        scale = E[i] + 2 * ME
-        assert abs(g[0] - o[0]) <= tol * scale, (i, E[i], g[0], o[0])
-        assert abs(g[4] - o[4]) <= tol * scale
-        if r == 1:  # primary momentum direction, weighted by its energy
-            assert np.abs(g[0] * g[1:4] - o[0] * o[1:4]).max() <= 10 * tol * scale, (i, E[i])
+        assert abs(g[4] - o[4]) <= tol * E[i], (i, E[i], g[4], o[4])  # local deposit
+        if r == 1:
+            kappa = E[i] if (ptype, proc) in DIFF_SURVIVOR else 0.0
+            assert abs(g[0] - o[0]) <= tol * max(o[0], kappa), (i, E[i], g[0], o[0])
+            assert np.abs(g[1:4] - o[1:4]).max() <= tol, (i, E[i], g[1:4], o[1:4])
         for j in range(int(o[5])):
             b = 6 + 5 * j
             assert int(g[b]) == int(o[b])
-            assert abs(g[b + 1] - o[b + 1]) <= tol * scale
-            assert np.abs(g[b + 1] * g[b + 2:b + 5] - o[b + 1] * o[b + 2:b + 5]).max() <= 10 * tol * scale, (i, j, E[i])
+            kappa = E[i] if (ptype, proc) == (0, 2) and int(o[b]) != 0 else 0.0
+            assert abs(g[b + 1] - o[b + 1]) <= tol * max(o[b + 1], kappa), (i, j, E[i], g[b + 1], o[b + 1])
+            assert np.abs(g[b + 2:b + 5] - o[b + 2:b + 5]).max() <= tol, (i, j, E[i], g[b + 2:b + 5], o[b + 2:b + 5])
+    assert cut_edge.mean() < 0.01, cut_edge.mean()
+    assert knife.mean() < 0.01, knife.mean()
     assert checked > 0.98 * n
 
 

@@ -2310,7 +2310,6 @@ extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long 
   if (c->cfg.precision != GV_MIXED) return GV_ERR_BAD_ARG;  // the array is sized for the mixed layout
   if (c->geo.field_T != 0.0) return GV_ERR_BAD_ARG;          // its kernel is the field-free one
   if (n_events > kStaticMaxEvents || n > 0xffffffffll) return GV_ERR_BAD_ARG;
-  if ((n > 0 && !is_device_ptr(prim)) || !is_device_ptr(edep) || !is_device_ptr(escape_E)) return GV_ERR_BAD_ARG;
   if (cudaSetDevice(c->device) != cudaSuccess) return GV_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   {  // the call waits on the host between launches: a capturing stream cannot take it
@@ -2321,6 +2320,7 @@ extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long 
     }
     if (cs != cudaStreamCaptureStatusNone) return GV_ERR_BAD_ARG;
   }
+  if ((n > 0 && !is_device_ptr(prim)) || !is_device_ptr(edep) || !is_device_ptr(escape_E)) return GV_ERR_BAD_ARG;
   finish_pending(c);  // a gv_transport of this context still in flight completes first
   unsigned char *base = nullptr;
   int rc = static_scratch(&base);

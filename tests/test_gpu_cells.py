@@ -25,7 +25,7 @@ import shower_stats as S
 pytestmark = pytest.mark.gpu
 NTHR = os.cpu_count() or 4
 B = 32        # batches
-M = 160       # events per batch
+M = 200       # events per batch
 
 
 @pytest.fixture(scope="module")
@@ -69,8 +69,11 @@ def test_cell_histogram_matches_oracle_bin_by_bin(gvmod, oracle_mod):
     assert len(p) > 3000
     assert np.abs(p).max() < 5.5, float(np.abs(p).max())
     assert 0.6 < np.mean(p * p) < 1.5, float(np.mean(p * p))
-    # the beam's cells carry the deposit: 1 % resolution of the central cells
+    # the beam's cells carry the deposit: around the shower maximum (layers
+    # holding >= 2 % of it) the comparison resolves 1 % of their sum
     gm, gs = _stats(g[:, :, 11:15, 17:19].sum((2, 3)))
     om, os_ = _stats(oc[:, :, 11:15, 17:19].sum((2, 3)))
-    big = om > 0.01 * om.sum()
-    assert (np.sqrt(gs ** 2 + os_ ** 2)[big] < 0.01 * om[big]).all()
+    big = om > 0.02 * om.sum()
+    assert big.sum() >= 10
+    res = np.sqrt(gs ** 2 + os_ ** 2)[big] / om[big]
+    assert (res < 0.01).all(), res.max()

@@ -3,7 +3,7 @@ allocate device memory during the call (frameworks that own a GPU's memory
 through their own pools).  It must give the same showers as gv_transport --
 identical integer histories, deposits equal up to the order of the FP64
 atomic sums -- on consecutive calls that reuse its fixed scratch array, and
-it must leave the device's free memory unchanged.
+it must leave the device's free memory and torch's allocator unchanged.
 
 This file is named so that pytest collects it last.
 """
@@ -27,21 +27,31 @@ def env():
     return torch, gv
 
 
-def _static_call(torch, gv, ctx, wl, seed):
-    """gv_transport_static through the C ABI with device buffers."""
+def _static_call(torch, gv, ctx, wl, seed, repeats=3):
+    """gv_transport_static through the C ABI with device buffers, `repeats`
+    times in a row (same inputs); returns the last call's results and the
+    smallest drop of the device's free memory seen across one call -- other
+    processes on a shared GPU can move it during any single call."""
     dev = torch.device("cuda")
     prim = torch.from_numpy(wl.primaries.view(np.uint8).copy()).to(dev)
     edep = torch.full((wl.n_events, ctx.n_subtotal), 7.0, dtype=torch.float64, device=dev)
     esc = torch.full((wl.n_events,), 7.0, dtype=torch.float64, device=dev)
     counters = (C.c_ulonglong * 16)()
-    torch.cuda.synchronize()
-    free0 = torch.cuda.mem_get_info()[0]
-    rc = ctx.lib.gv_transport_static(ctx.h, prim.data_ptr(), len(wl.primaries), wl.n_events,
-                                     C.c_ulonglong(seed), torch.cuda.current_stream().cuda_stream,
-                                     edep.data_ptr(), esc.data_ptr(), counters)
-    torch.cuda.synchronize()
-    free1 = torch.cuda.mem_get_info()[0]
-    return rc, edep.cpu().numpy(), esc.cpu().numpy(), list(counters), free0 - free1
+    stream = torch.cuda.current_stream().cuda_stream
+    used = []
+    for _ in range(repeats):
+        torch.cuda.synchronize()
+        alloc0, res0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
+        free0 = torch.cuda.mem_get_info()[0]
+        rc = ctx.lib.gv_transport_static(ctx.h, prim.data_ptr(), len(wl.primaries), wl.n_events,
+                                         C.c_ulonglong(seed), stream, edep.data_ptr(), esc.data_ptr(), counters)
+        torch.cuda.synchronize()
+        used.append(free0 - torch.cuda.mem_get_info()[0])
+        # nothing went through torch's allocator either
+        assert torch.cuda.memory_allocated() == alloc0 and torch.cuda.memory_reserved() == res0
+        # gv_sync reports this call's status
+        assert ctx.lib.gv_sync(ctx.h, stream) == rc
+    return rc, edep.cpu().numpy(), esc.cpu().numpy(), list(counters), min(used)
 
 
 def _reference(ctx, wl, seed):
@@ -71,7 +81,7 @@ def test_static_transport_matches_allocating_transport_twice(env):
         scale = np.maximum(ref["edep"].sum(1, keepdims=True), 1.0)
         assert (np.abs(edep - ref["edep"]) / scale).max() < 1e-9
         assert np.abs(esc - ref["escape"]).max() < 1e-9 * max(1.0, ref["escape"].max())
-        assert used == 0  # the call took no device memory
+        assert used <= 0  # the call took no device memory
 
 
 def test_static_transport_rejects_what_it_cannot_hold(env):
@@ -93,3 +103,43 @@ def test_static_transport_rejects_what_it_cannot_hold(env):
     ctx64 = gv.Context(wl, gv.gv_default_config(precision=gv.GV_FP64, stack_capacity=1 << 16))
     assert ctx64.lib.gv_transport_static(ctx64.h, prim.data_ptr(), 4, 4, 1, s, edep.data_ptr(),
                                          esc.data_ptr(), counters) == -1
+
+
+def test_static_transport_caps_events_in_flight_for_10GeV(env):
+    """64 showers of 10 GeV e- in Pb/polystyrene: the events in flight follow
+    the automatic cap (65,536 / (0.15 x 10,000 + 64) = 41 events), so the
+    scratch queues hold them; energy is conserved over the batch."""
+    torch, gv = env
+    wl = W.pbps_electrons(64, 10_000.0)
+    ctx = gv.Context(wl, gv.gv_default_config(stack_capacity=1 << 16))
+    rc, edep, esc, cnt, used = _static_call(torch, gv, ctx, wl, wl.seed, repeats=1)
+    assert rc == 0, gv.load().gv_strerror(rc)
+    ME = 0.51099895
+    tot = edep.sum() + esc.sum()
+    want = 64 * 10_000.0 + 2 * ME * (cnt[8] - cnt[7])
+    assert abs(tot - want) < 1e-6 * want
+    assert cnt[15] <= 1 << 16  # peak live tracks within one queue's capacity
+
+
+def test_static_transport_refuses_a_capturing_stream(env):
+    """The call waits on the host between its launches, so a stream under
+    capture is refused before anything is queued on it."""
+    torch, gv = env
+    wl = W.pbps_electrons(4, 100.0)
+    ctx = gv.Context(wl, gv.gv_default_config(stack_capacity=1 << 16))
+    dev = torch.device("cuda")
+    prim = torch.from_numpy(wl.primaries.view(np.uint8).copy()).to(dev)
+    edep = torch.zeros((4, ctx.n_subtotal), dtype=torch.float64, device=dev)
+    esc = torch.zeros(4, dtype=torch.float64, device=dev)
+    counters = (C.c_ulonglong * 16)()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
+        rc = ctx.lib.gv_transport_static(ctx.h, prim.data_ptr(), 4, 4, 1, s.cuda_stream, edep.data_ptr(),
+                                         esc.data_ptr(), counters)
+        edep.add_(1.0)  # the capture records something
+    assert rc == -1
+    torch.cuda.synchronize()
+    rc, _, _, _, _ = _static_call(torch, gv, ctx, wl, 1, repeats=1)
+    assert rc == 0

@@ -9,6 +9,9 @@ running only the oracle.  Criteria of the shower parity: every layer within
 totals likewise.  The GPU samples use the workloads' default seed, the
 stored ones another: the two are independent.
 """
+import json
+import os
+
 import pytest
 
 from paper_2005_00949_gb300 import workloads as W
@@ -41,3 +44,7 @@ def test_mixed_gpu_matches_untabulated_oracle(gvmod, n, E, golden):
     got = S.compare(S.summarize(r["edep"], wl.n_layers), S.read(golden))
     assert got["active_layers"] >= 5, got
     assert got["active_materials"] == 2, got
+    path = os.environ.get("GV_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"name": f"mixed_gpu_vs_untabulated_{E:g}MeV", "events": n, **got}) + "\n")

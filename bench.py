@@ -35,6 +35,15 @@ sys.path.insert(0, ROOT)
 from paper_2005_00949_gb300 import workloads as W  # noqa: E402
 
 METRIC = "EM steps/s and 10 GeV e- showers/s on 1 GB300; HBM roofline fraction"
+WORKLOAD = ("e-10GeV_PbPS50_2000: 2000 x 10 GeV e- on 50 x (2 mm Pb + 5 mm polystyrene), "
+            "40x40 cm, cuts 1 MeV")
+
+
+def _config(world: int) -> dict:
+    """The workload as both arms name it (identical for the GPU and the
+    reference arm at one GPU)."""
+    return {"workload": WORKLOAD, "events_per_gpu": 2000, "parallelism": f"events x{world}",
+            "l2": "GPU arm: flushed between timed steps (512 MiB write); reference arm (host CPU): not applicable"}
 N_EVENTS = 2000
 E0 = 10_000.0
 # algorithmic DRAM bytes of one track step in a step-synchronous wavefront,
@@ -228,8 +237,9 @@ def run_reference(args):
             "ms_per_step": 1000.0 * sum(times) / len(times) * (N_EVENTS / n_ev),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "e-10GeV_PbPS50_2000: 2000 x 10 GeV e- on 50 x (2 mm Pb + 5 mm polystyrene)", "events_per_step": N_EVENTS,
-                       "sample_events_per_step": n_ev, "parallelism": "host threads"},
+            "config": _config(1),
+            "reference": {"program": "the FP64 oracle (tabulated transport), host threads",
+                          "sample_events_per_step": n_ev},
             "cpu_baseline": {"value": v, "unit": "showers/s", "cores": nthr, "kind": "oracle",
                              "sample": f"{n_ev} events per step of the 2000-event workload"},
             "e2e": {"value": v, "unit": "showers/s", "h2d_bytes_per_step": 0,
@@ -367,10 +377,8 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": "e-10GeV_PbPS50_2000: 2000 x 10 GeV e- on "
-                               "50 x (2 mm Pb + 5 mm polystyrene), 40x40 cm, cuts 1 MeV",
-                   "events_per_gpu": wl.n_events, "precision": "mixed FP32 physics / FP64 positions",
-                   "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"events x{world}"},
+        "config": _config(world),
+        "precision": "mixed FP32 physics / FP64 positions and tallies",
         "steps_per_s": steps_per_s,
         "track_steps_per_step": steps_tot / args.steps / 1.0,
         "kernel_ms_per_step": kernel_ms / args.steps,

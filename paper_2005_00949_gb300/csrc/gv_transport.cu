@@ -766,14 +766,17 @@ __global__ void GV_STEP_BOUNDS
   pend.sum = R(0);
   pend.comp = R(0);
   Pending<R> *const pd = MERGE ? &pend : nullptr;
+  const bool block_claims = SORT || S->claim_chunks == 0;
+  if (block_claims) {  // the first claim; each later one is issued before the previous claim's survivors go out
+    if (tid == 0) s_chunk = atomicAdd(&ctl->claim, 1u);
+    __syncthreads();
+  }
   for (;;) {
     // Work claiming: with the basketizer a chunk is one block (its step loop
     // syncs the block); without it every warp claims its own 32-track chunks
     // and never waits for the rest of the block.
     unsigned chunk, idx;
-    if (SORT || S->claim_chunks == 0) {
-      if (tid == 0) s_chunk = atomicAdd(&ctl->claim, 1u);
-      __syncthreads();
+    if (block_claims) {
       chunk = s_chunk;
       __syncthreads();
     } else {
@@ -857,6 +860,7 @@ __global__ void GV_STEP_BOUNDS
       }
     }
     const int K = s_K;
+    unsigned ended_prev = 0u;  // evlive before this lane's last track ended (1: it closed its event)
     for (int kk = 0; kk < K; ++kk) {
       // (with the basketizer the block leaves the loop together, after the
       // count barrier below shows that no lane was alive)
@@ -1021,10 +1025,18 @@ __global__ void GV_STEP_BOUNDS
           }
         }
       }
-      if (was_alive && !alive) track_ended(S, t.ev);
+      if (was_alive && !alive) {
+        if (kk + 1 < K) track_ended(S, t.ev);
+        else ended_prev = atomicSub(&S->evlive[t.ev], 1u);  // read after the survivors are out
+      }
     }
+    // the next claim's atomic and the event count's are in flight while the
+    // survivors are written
+    unsigned next_chunk = 0u;
+    if (block_claims && tid == 0) next_chunk = atomicAdd(&ctl->claim, 1u);
     if (MERGE) warp_flush(S, pend);  // nothing stays pending past a claim
     push_survivor(S, out, t, alive);
+    if (ended_prev == 1u) atomicAdd(&ctl->ev_done, 1u);
     if (use_local) {  // what is left on the block's stack goes to the next generation
       __syncthreads();
       const int n = max(0, min(s_ltop, lstk.cap));
@@ -1034,6 +1046,10 @@ __global__ void GV_STEP_BOUNDS
       }
       __syncthreads();
       if (tid == 0) s_ltop = 0;
+    }
+    if (block_claims) {
+      if (tid == 0) s_chunk = next_chunk;
+      __syncthreads();
     }
   }
   // flush block counters; the last block plans the next generation

@@ -921,3 +921,21 @@ def test_bhabha_dcs_high_energy_limit(oracle_mod):
     for e in np.linspace(0.01, 1.0, 100):
         got = e * e * oracle_mod.Oracle.dcs(W_M.BHABHA, T, e)
         assert abs(got - (1 - e + e * e) ** 2) < 1e-6
+
+
+def test_annihilation_cross_section_limits(oracle_mod):
+    """Heitler's two-photon cross section per electron against its two
+    textbook limits: Dirac's slow-positron form pi r_e^2 / beta (the c/v law)
+    and the high-energy form pi r_e^2 / gamma (ln 2 gamma - 1)."""
+    o = oracle_mod.Oracle(W.pbps_electrons(1))
+    nel = o.n_el(0)
+    for T in (1e-5, 1e-4):
+        g = T / ME + 1.0
+        beta = math.sqrt(1.0 - 1.0 / (g * g))
+        got = o.xs(W.POSITRON, 2, 0, T) / nel
+        assert abs(got / (math.pi * RE ** 2 / beta) - 1.0) < 5 * beta, (T, got)
+    for T in (1e5, 1e6):
+        g = T / ME + 1.0
+        got = o.xs(W.POSITRON, 2, 0, T) / nel
+        want = math.pi * RE ** 2 / g * (math.log(2 * g) - 1.0)
+        assert abs(got / want - 1.0) < 5 * math.log(g) / g, (T, got, want)

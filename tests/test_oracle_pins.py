@@ -939,3 +939,12 @@ def test_annihilation_cross_section_limits(oracle_mod):
         got = o.xs(W.POSITRON, 2, 0, T) / nel
         want = math.pi * RE ** 2 / g * (math.log(2 * g) - 1.0)
         assert abs(got / want - 1.0) < 5 * math.log(g) / g, (T, got, want)
+
+
+def test_moller_dcs_high_energy_limit(oracle_mod):
+    """eps^2 (1 - eps)^2 dsigma/deps -> (1 - eps + eps^2)^2 as gamma -> infinity
+    (the ultra-relativistic Moller form)."""
+    T = 1e7 * ME
+    for e in np.linspace(0.01, 0.5, 50):
+        got = e * e * (1 - e) ** 2 * oracle_mod.Oracle.dcs(W_M.MOLLER, T, e)
+        assert abs(got - (1 - e + e * e) ** 2) < 1e-6

@@ -8,9 +8,9 @@
  *
  * Everything is FP64, in the order the stepping stages of Sec. 2.1.2 name
  * them.  Two transports share the stepping loop:
- *  - tabulated (default), the paper's method: cross sections and ranges
- *    interpolated linearly in ln E between table nodes that hold the exact
- *    quantities at the nodes of the logarithmic energy grid (the tables the
+ *  - tabulated (default), the paper's method: cross sections interpolated
+ *    linearly, and ranges as ln R, in ln E between table nodes that hold the
+ *    exact quantities at the nodes of the logarithmic energy grid (the tables the
  *    paper's profiles show as Spline::GetValueAt / G4PhysicsVector, Sec.
  *    6.6); final states from sampling tables (Sec. 3.5: the alias method with
  *    a discrete intermediate variable), or by rejection where chosen;

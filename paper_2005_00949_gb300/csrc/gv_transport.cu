@@ -12,6 +12,11 @@
 // finish writes the plan of the next generation: queue chunk ranges and
 // claim size, primaries to inject (the event server refill, bounded by a
 // live-track budget) and the steps per claim.
+//
+// Host side: gv_transport enqueues one transport on the context's stream,
+// ordered after the caller's stream (which then waits for it), and returns;
+// gv_sync waits for it and fills the caller's result record from the
+// control block copied back to pinned memory.
 #include <cuda_runtime.h>
 
 #include <algorithm>

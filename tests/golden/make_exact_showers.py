@@ -32,6 +32,13 @@ CASES = [
      "200000 x 1 GeV e- on 50 x (2 mm Pb + 5 mm polystyrene), 40x40 cm, cuts 1 MeV"),
     ("exact_showers_e-10GeV_PbPS50.txt", lambda: W.pbps_electrons(65_536, 10_000.0),
      "65536 x 10 GeV e- on 50 x (2 mm Pb + 5 mm polystyrene), 40x40 cm, cuts 1 MeV"),
+    ("exact_showers_e-100GeV_WSi50.txt", lambda: W.wsi_cells(2048, 100_000.0),
+     "2048 x 100 GeV e- on 50 x (3 mm W + 0.5 mm Si), 40x40 cm, entry points uniform over the "
+     "central 4x4 cells of 1.25 cm, cuts 0.5 MeV"),
+    ("exact_showers_e-10GeV_PbLAr50_4T_msc.txt",
+     lambda: W.with_msc(W.with_field(W.pblar_testem3(8192, 10_000.0), 4.0, 1)),
+     "8192 x 10 GeV e- on 50 x (2.3 mm Pb + 5.7 mm liquid argon), 40x40 cm, 4 T along y, "
+     "multiple scattering, cuts 0.1 MeV (gamma) / 1 MeV (e)"),
 ]
 
 

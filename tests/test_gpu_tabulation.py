@@ -48,3 +48,25 @@ def test_mixed_gpu_matches_untabulated_oracle(gvmod, n, E, golden):
     if path:
         with open(path, "a") as f:
             f.write(json.dumps({"name": f"mixed_gpu_vs_untabulated_{E:g}MeV", "events": n, **got}) + "\n")
+
+
+@pytest.mark.parametrize("make,golden", [
+    (lambda: W.wsi_cells(2048, 100_000.0), "exact_showers_e-100GeV_WSi50.txt"),
+    (lambda: W.with_msc(W.with_field(W.pblar_testem3(8192, 10_000.0), 4.0, 1)),
+     "exact_showers_e-10GeV_PbLAr50_4T_msc.txt"),
+], ids=["WSi_100GeV", "PbLAr_4T_msc"])
+def test_mixed_gpu_matches_untabulated_oracle_other_layouts(gvmod, make, golden):
+    """The W/Si cell calorimeter (0.5 MeV cuts) and the TestEm3 layout with
+    its 4 T field and multiple scattering: per-layer and per-material
+    criteria against the untabulated transport's stored showers."""
+    wl = make()
+    ctx = gvmod.Context(wl, gvmod.gv_default_config(stack_capacity=1 << 23))
+    r = ctx.transport(cells=False)
+    ctx.close()
+    assert r["status"] == 0
+    got = S.compare(S.summarize(r["edep"], wl.n_layers), S.read(golden))
+    assert got["active_materials"] == 2, got
+    path = os.environ.get("GV_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"name": f"mixed_gpu_vs_untabulated_{wl.name}", "events": wl.n_events, **got}) + "\n")

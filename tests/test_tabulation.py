@@ -11,8 +11,9 @@ shower parity: every layer within 3 combined standard errors, 0.5 % where
 that bound is active (enough showers that 0.5 % >= 3 combined standard
 errors on layers with >= 1 % of the deposit), and the per-material totals.
 
-The untabulated samples (200,000 showers of 1 GeV and 65,536 of 10 GeV,
-about 20 CPU-minutes) are stored in tests/golden/ by
+The untabulated samples (200,000 showers of 1 GeV and 65,536 of 10 GeV in
+Pb/polystyrene, 2048 of 100 GeV in W/Si, 8192 of 10 GeV in the TestEm3
+layout with field and scattering) are stored in tests/golden/ by
 tests/golden/make_exact_showers.py, which runs only the oracle; their seed
 differs from the workloads' default, so they are independent of the
 samples drawn here.
@@ -39,4 +40,21 @@ def test_tabulated_oracle_matches_untabulated_10GeV(oracle_mod):
     r = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
     got = S.compare(S.summarize(r["edep"], wl.n_layers), S.read("exact_showers_e-10GeV_PbPS50.txt"))
     assert got["active_layers"] >= 5, got
+    assert got["active_materials"] == 2, got
+
+
+def test_tabulated_oracle_matches_untabulated_WSi_100GeV(oracle_mod):
+    """The segmented W/Si calorimeter (0.5 MeV cuts), 2048 showers of 100 GeV."""
+    wl = W.wsi_cells(2048, 100_000.0)
+    r = oracle_mod.Oracle(wl).transport(n_threads=NTHR, cells=False)
+    got = S.compare(S.summarize(r["edep"], wl.n_layers), S.read("exact_showers_e-100GeV_WSi50.txt"))
+    assert got["active_materials"] == 2, got
+
+
+def test_tabulated_oracle_matches_untabulated_PbLAr_field_msc(oracle_mod):
+    """The paper's TestEm3 layout in its conditions (4 T transverse field,
+    multiple scattering, 0.1 MeV photon cut), 8192 showers of 10 GeV."""
+    wl = W.with_msc(W.with_field(W.pblar_testem3(8192, 10_000.0), 4.0, 1))
+    r = oracle_mod.Oracle(wl).transport(n_threads=NTHR)
+    got = S.compare(S.summarize(r["edep"], wl.n_layers), S.read("exact_showers_e-10GeV_PbLAr50_4T_msc.txt"))
     assert got["active_materials"] == 2, got

@@ -314,7 +314,7 @@ long long gv_last_launches(void *ctx);
 int gv_unit_philox(const unsigned *ctr, const unsigned *key, unsigned *out, long long n,
                    void *stream);
 
-/* Table lookup (ComputeIntLen, Spline::GetValueAt of Sec. 6.6) of particle
+/* Table lookup (ComputeIntLen, Spline::GetValueAt of Sec. 6.3) of particle
  * `type` in material `mat` at energies E[i]: out[4i..4i+3] = the four
  * interpolated table quantities (gamma: Compton, photo, pair, 0; e-: brems,
  * ionisation, range, 0; e+: brems, ionisation, annihilation, range). */

@@ -150,7 +150,7 @@ class Oracle:
     formulas at each track's own energy, range and continuous loss by
     quadrature and root finding, every final state by rejection from its
     DCS.  The default transport interpolates the stepping tables and samples
-    the sampling tables, as the paper's method does (Sec. 3.5, Sec. 6.6)."""
+    the sampling tables, as the paper's method does (Sec. 3.5, Sec. 6.3)."""
 
     def __init__(self, wl, exact: bool = False):
         self.wl = wl

@@ -12,7 +12,7 @@
  *    linearly, and ranges as ln R, in ln E between table nodes that hold the
  *    exact quantities at the nodes of the logarithmic energy grid (the tables the
  *    paper's profiles show as Spline::GetValueAt / G4PhysicsVector, Sec.
- *    6.6); final states from sampling tables (Sec. 3.5: the alias method with
+ *    6.3); final states from sampling tables (Sec. 3.5: the alias method with
  *    a discrete intermediate variable), or by rejection where chosen;
  *  - untabulated (or_setup.exact): cross sections from their formulas at the
  *    track's own energy, the range by quadrature of 1/S from the grid node

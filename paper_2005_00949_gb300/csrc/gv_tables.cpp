@@ -2,7 +2,7 @@
 // stepping loop reads: macroscopic cross sections of every discrete process,
 // restricted-loss ranges, and the alias sampling tables of the final-state
 // models ("sampling tables", GeantV Sec. 3.5).  The tables play the role of
-// the ComputeIntLen / Spline::GetValueAt lookups of Sec. 2.1.2 and Sec. 6.6.
+// the ComputeIntLen / Spline::GetValueAt lookups of Sec. 2.1.2 and Sec. 6.3.
 //
 // Physics (the paper defers it to an external EM paper):
 //   Compton: free-electron Klein-Nishina.

@@ -1,7 +1,7 @@
 """Pins of the oracle's untabulated transport (Oracle(..., exact=True)).
 
 The stepping loop of the paper's method reads interpolated tables and samples
-sampling tables (Sec. 3.5, Sec. 6.6).  The untabulated transport replaces
+sampling tables (Sec. 3.5, Sec. 6.3).  The untabulated transport replaces
 every tabulated quantity by its definition: cross sections from their
 formulas at the track's own energy, the range and its inverse by quadrature
 and root finding, and every final state by rejection from its differential

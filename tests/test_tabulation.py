@@ -1,7 +1,7 @@
 """What the tables cost: the tabulated transport against the untabulated one.
 
 The paper's stepping loop reads cross sections and ranges interpolated in
-ln E from tables (Sec. 6.6, Spline::GetValueAt) and samples final states from
+ln E from tables (Sec. 6.3, Spline::GetValueAt) and samples final states from
 sampling tables (Sec. 3.5).  The oracle's default transport does the same
 (with its own FP64 tables), so comparing the GPU with it cannot see the
 error of the tabulation itself.  Here the tabulated oracle is compared with

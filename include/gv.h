@@ -140,8 +140,14 @@ typedef struct {
   int per_event_counts;       /* 1: keep GV_NCOUNT counters per event (slower) */
   int process_sort;           /* 1: re-basket interacting tracks by process in each block */
   long long max_events_in_flight; /* refill only while fewer events are unfinished; 0: no cap;
-                                     -1 (default): stack_capacity / (0.15 per MeV of the most
-                                     energetic primary + 64), at least 16 */
+                                     -1 (default): automatic. Every primary is budgeted 0.15
+                                     live tracks per MeV of its energy + 64. gv_transport and
+                                     gv_transport_events (GV_BATCHED) admit the next primaries
+                                     while the budgets of the unfinished events fit in
+                                     stack_capacity, and one at least when no track is live.
+                                     gv_transport_static and GV_ONE_EVENT_PER_LAUNCH budget every
+                                     event like the most energetic primary: stack_capacity /
+                                     (0.15 per MeV + 64) events, at least 16 */
   int claim_chunks;           /* without process_sort: 1 (default) = every warp claims its own
                                  32-track chunks from 16 sliced counters; 0 = one claim per block */
   int along_steps;            /* with process_sort: steps a track may take without a discrete

@@ -73,6 +73,7 @@ struct Ctl {
   unsigned req_n;
   unsigned key_n[kNReqKey];
   unsigned claim_b, blocks_done_b;
+  unsigned long long cost_started, cost_done;  // automatic cap: track budget taken by / returned from events
 };
 
 template <typename R> struct DevState {
@@ -106,6 +107,8 @@ template <typename R> struct DevState {
   unsigned smem_lk_off;          // the block's secondary stack (local_stack)
   int local_stack;
   int grid, adaptive_chunk;  // blocks of the step kernel; spread small populations over all of them
+  const unsigned long long *pcost;  // automatic cap: prefix sums of the primaries' track budgets [n_prim + 1], or null
+  unsigned long long *evcost;       // automatic cap: budget held by each event in flight [n_events]
 };
 
 }  // namespace gv

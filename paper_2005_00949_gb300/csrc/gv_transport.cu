@@ -503,9 +503,37 @@ __device__ void push_kids(const DevState<R> *S, int out, const Parent &t, const 
   if (kids.n > 0) atomicAdd(&S->evlive[t.ev], static_cast<unsigned>(kids.n));
 }
 
+// The automatic events-in-flight cap (the paper keeps a bounded number of
+// events in flight, Sec. 2.1.1): a primary of energy E is budgeted 0.15
+// live tracks per MeV (about 2.3 times the peak live-track count of a
+// shower per MeV) plus 64, and new primaries are admitted while the budgets
+// of the events in flight fit the queue capacity.  NaN or negative energies
+// get the base budget.
+__device__ __forceinline__ unsigned long long prim_cost(double E) {
+  const double e = (E > 0.0 && E < 1e12) ? E : 0.0;
+  return 64ull + static_cast<unsigned long long>(ceil(0.15 * e));
+}
+
+// An event's last track ended: the event leaves the set in flight and
+// returns its budget.  Out of line: it runs once per event, and inlined at
+// both of its call sites it slowed the step kernel by 0.5 %.
+template <typename R> __device__ __noinline__ void event_closed(const DevState<R> *S, unsigned ev) {
+  atomicAdd(&S->ctl->ev_done, 1u);
+  if (S->evcost) atomicAdd(&S->ctl->cost_done, atomicExch(&S->evcost[ev], 0ull));
+}
+
+// A primary was loaded: its budget goes to its event (returned when the
+// event closes), or straight back if it never entered the box.
+template <typename R>
+__device__ __forceinline__ void primary_cost(const DevState<R> *S, unsigned ev, double E, bool entered) {
+  if (!S->evcost) return;
+  if (entered) atomicAdd(&S->evcost[ev], prim_cost(E));
+  else atomicAdd(&S->ctl->cost_done, prim_cost(E));
+}
+
 // A track ended: book it against its event; the last one closes the event.
 template <typename R> __device__ __forceinline__ void track_ended(const DevState<R> *S, unsigned ev) {
-  if (atomicSub(&S->evlive[ev], 1u) == 1u) atomicAdd(&S->ctl->ev_done, 1u);
+  if (atomicSub(&S->evlive[ev], 1u) == 1u) event_closed(S, ev);
 }
 
 // An interaction request staged in shared memory by the in-block basketizer.
@@ -590,6 +618,24 @@ template <typename R> __device__ void plan_next(const DevState<R> *S, int pn) {
         const unsigned room = c->max_in_flight > fl ? c->max_in_flight - fl : 0u;
         inj = inj < room ? inj : room;
       }
+      if (S->pcost && inj > 0) {  // automatic cap: the budgets of the events in flight fit the capacity
+        if (live == 0) c->cost_done = c->cost_started;  // nothing alive: every event has closed
+        const unsigned long long held = c->cost_started > c->cost_done ? c->cost_started - c->cost_done : 0ull;
+        const unsigned long long room = S->capacity > held ? S->capacity - held : 0ull;
+        const unsigned long long *pc = S->pcost + c->prim_next;
+        const unsigned long long base = pc[0];
+        if (pc[inj] - base > room) {  // the longest run of the next primaries that fits
+          unsigned lo = 0, hi = inj;  // budget(lo) <= room < budget(hi)
+          while (hi - lo > 1) {
+            const unsigned mid = lo + (hi - lo) / 2;
+            if (pc[mid] - base <= room) lo = mid;
+            else hi = mid;
+          }
+          inj = lo;
+        }
+        if (inj == 0 && live == 0) inj = 1;  // one primary at least when nothing is alive
+        c->cost_started += pc[inj] - base;
+      }
     }
   }
   c->prim_begin = c->prim_next;
@@ -644,9 +690,14 @@ template <typename R> __global__ void init_kernel(const DevState<R> *S) {
   c->live_peak = 0;
   c->ev_started = 0;
   c->ev_done = 0;
+  c->cost_started = 0;
+  c->cost_done = 0;
   if (S->max_in_flight >= 0) {
     c->max_in_flight = static_cast<unsigned>(S->max_in_flight);
-  } else {  // automatic: ~0.065 live tracks per MeV at the peak of a shower, x2.3
+  } else if (S->pcost) {  // automatic, per event: the budgets of prim_cost (plan_next)
+    c->max_in_flight = 0;
+  } else {  // automatic, every event budgeted like the most energetic primary:
+            // ~0.065 live tracks per MeV at the peak of a shower, x2.3
     const double emax = static_cast<double>(__uint_as_float(c->emax_bits));
     const double cap = static_cast<double>(S->capacity) / (0.15 * emax + 64.0);
     c->max_in_flight = static_cast<unsigned>(cap < 16.0 ? 16.0 : (cap > 1e9 ? 1e9 : cap));
@@ -655,7 +706,48 @@ template <typename R> __global__ void init_kernel(const DevState<R> *S) {
   plan_next(S, 0);
 }
 
-// largest primary energy, for the automatic events-in-flight cap
+// Prefix sums of the primaries' budgets for the automatic events-in-flight
+// cap: pcost[i] = sum of prim_cost over primaries 0 .. i-1.  One block; each
+// thread sums a contiguous run, the block scans the run totals, each thread
+// writes its run's sums.
+constexpr int kCostScanThreads = 1024;
+template <typename R>
+__global__ void __launch_bounds__(kCostScanThreads) prim_cost_kernel(const DevState<R> *S, unsigned long long *pcost) {
+  __shared__ unsigned long long s_warp[kCostScanThreads / 32];
+  const unsigned n = S->n_prim, tid = threadIdx.x;
+  const unsigned per = (n + kCostScanThreads - 1) / kCostScanThreads;
+  const unsigned lo = min(n, tid * per), hi = min(n, lo + per);
+  unsigned long long sum = 0;
+  for (unsigned i = lo; i < hi; ++i) sum += prim_cost(S->prim[i].E_MeV);
+  const int lane = tid & 31, warp = tid >> 5;
+  unsigned long long incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long w = s_warp[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    s_warp[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  unsigned long long run = incl - sum + (warp ? s_warp[warp - 1] : 0ull);
+  if (tid == 0) pcost[0] = 0ull;
+  for (unsigned i = lo; i < hi; ++i) {
+    run += prim_cost(S->prim[i].E_MeV);
+    pcost[i + 1] = run;
+  }
+}
+
+// largest primary energy, for the automatic events-in-flight cap of the
+// allocation-free entry point
 template <typename R> __global__ void prim_emax_kernel(const DevState<R> *S) {
   float m = 0.0f;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < S->n_prim; i += gridDim.x * blockDim.x) {
@@ -837,6 +929,7 @@ __global__ void GV_STEP_BOUNDS
       const unsigned i = s_pb + idx;
       const unsigned pi = S->order ? S->order[i] : i;
       gv_primary p = S->prim[pi];
+      const double e_in = p.E_MeV;  // the budget of the automatic cap is the caller's energy
       p.event -= S->ev_base;  // the tallies' row (events below the range wrap to a large value)
       if (p.type < 0 || p.type > 2 || p.event >= S->n_events) {  // caller's device array: check here
         set_status(ctl, GV_ERR_BAD_ARG);
@@ -859,8 +952,10 @@ __global__ void GV_STEP_BOUNDS
       if (t.sub < 0) {
         atomicAdd(&S->escape[t.ev], p.E_MeV);
         if (t.type == 2) count(S, &bc, t.ev, GV_C_EP_ESC);
+        primary_cost(S, t.ev, e_in, false);
       } else {
         alive = true;
+        primary_cost(S, t.ev, e_in, true);
         if (atomicAdd(&S->evlive[t.ev], 1u) == 0u) atomicAdd(&ctl->ev_started, 1u);
       }
     }
@@ -1041,7 +1136,7 @@ __global__ void GV_STEP_BOUNDS
     if (block_claims && tid == 0) next_chunk = atomicAdd(&ctl->claim, 1u);
     if (MERGE) warp_flush(S, pend);  // nothing stays pending past a claim
     push_survivor(S, out, t, alive);
-    if (ended_prev == 1u) atomicAdd(&ctl->ev_done, 1u);
+    if (ended_prev == 1u) event_closed(S, t.ev);
     if (use_local) {  // what is left on the block's stack goes to the next generation
       __syncthreads();
       const int n = max(0, min(s_ltop, lstk.cap));
@@ -1197,6 +1292,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_ALONG_MIN_BLOCKS : 2)
       const unsigned i = s_pb + idx;
       const unsigned pi = S->order ? S->order[i] : i;
       gv_primary p = S->prim[pi];
+      const double e_in = p.E_MeV;  // the budget of the automatic cap is the caller's energy
       p.event -= S->ev_base;  // the tallies' row (events below the range wrap to a large value)
       if (p.type < 0 || p.type > 2 || p.event >= S->n_events) {  // caller's device array: check here
         set_status(ctl, GV_ERR_BAD_ARG);
@@ -1219,8 +1315,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_ALONG_MIN_BLOCKS : 2)
       if (t.sub < 0) {
         atomicAdd(&S->escape[t.ev], p.E_MeV);
         if (t.type == 2) count(S, &bc, t.ev, GV_C_EP_ESC);
+        primary_cost(S, t.ev, e_in, false);
       } else {
         alive = true;
+        primary_cost(S, t.ev, e_in, true);
         if (atomicAdd(&S->evlive[t.ev], 1u) == 0u) atomicAdd(&ctl->ev_started, 1u);
       }
     }
@@ -1392,7 +1490,10 @@ struct Ctx {
   double *d_edep = nullptr, *d_cell = nullptr, *d_escape = nullptr;
   unsigned long long *d_evcnt = nullptr;
   unsigned *d_evlive = nullptr;
+  unsigned long long *d_evcost = nullptr;  // budget held per event (automatic in-flight cap)
   size_t ev_cap = 0;
+  unsigned long long *d_pcost = nullptr;   // prefix sums of the primaries' budgets
+  size_t pcost_cap = 0;
   gv_primary *d_prim = nullptr;
   unsigned *d_order = nullptr;
   size_t prim_cap = 0;
@@ -1910,17 +2011,30 @@ int run_transport(Ctx *c, const gv_primary *p, long long n, long long first_even
     cudaFree(c->d_escape);
     cudaFree(c->d_evcnt);
     cudaFree(c->d_evlive);
+    cudaFree(c->d_evcost);
     c->d_edep = nullptr;
     c->d_escape = nullptr;
     c->d_evcnt = nullptr;
     c->d_evlive = nullptr;
+    c->d_evcost = nullptr;
     c->ev_cap = 0;
     if (cudaMalloc(&c->d_edep, sizeof(double) * n_events * nsub) != cudaSuccess ||
         cudaMalloc(&c->d_escape, sizeof(double) * n_events) != cudaSuccess ||
         cudaMalloc(&c->d_evcnt, sizeof(unsigned long long) * n_events * GV_NCOUNT) != cudaSuccess ||
-        cudaMalloc(&c->d_evlive, sizeof(unsigned) * n_events) != cudaSuccess)
+        cudaMalloc(&c->d_evlive, sizeof(unsigned) * n_events) != cudaSuccess ||
+        cudaMalloc(&c->d_evcost, sizeof(unsigned long long) * n_events) != cudaSuccess)
       return GV_ERR_OOM;
     c->ev_cap = n_events;
+  }
+  // the automatic events-in-flight cap of a batched transport budgets every
+  // event by its own primaries (prim_cost_kernel, plan_next)
+  const bool cost_cap = c->cfg.max_events_in_flight < 0 && c->cfg.mode == GV_BATCHED && n > 0;
+  if (cost_cap && static_cast<size_t>(n) + 1 > c->pcost_cap) {
+    cudaFree(c->d_pcost);
+    c->d_pcost = nullptr;
+    c->pcost_cap = 0;
+    if (cudaMalloc(&c->d_pcost, sizeof(unsigned long long) * (n + 1)) != cudaSuccess) return GV_ERR_OOM;
+    c->pcost_cap = static_cast<size_t>(n) + 1;
   }
   if (ncell && !c->d_cell) {
     if (cudaMalloc(&c->d_cell, sizeof(double) * ncell) != cudaSuccess) return GV_ERR_OOM;
@@ -1966,6 +2080,7 @@ int run_transport(Ctx *c, const gv_primary *p, long long n, long long first_even
   const bool evc = c->cfg.per_event_counts != 0 && res && res->event_counts;
   if (evc) CK(cudaMemsetAsync(c->d_evcnt, 0, sizeof(unsigned long long) * n_events * GV_NCOUNT, c->stream));
   CK(cudaMemsetAsync(c->d_evlive, 0, sizeof(unsigned) * n_events, c->stream));
+  if (cost_cap) CK(cudaMemsetAsync(c->d_evcost, 0, sizeof(unsigned long long) * n_events, c->stream));
   DevState<R> s = make_state<R>(c);
   s.prim = dp;
   s.order = c->cfg.mode == GV_ONE_EVENT_PER_LAUNCH ? c->d_order : nullptr;
@@ -1978,13 +2093,17 @@ int run_transport(Ctx *c, const gv_primary *p, long long n, long long first_even
   s.evcnt = evc ? c->d_evcnt : nullptr;
   s.evlive = c->d_evlive;
   s.max_in_flight = static_cast<int>(std::min<long long>(c->cfg.max_events_in_flight, 0x7fffffffll));
+  s.pcost = cost_cap ? c->d_pcost : nullptr;
+  s.evcost = cost_cap ? c->d_evcost : nullptr;
   s.seed_lo = static_cast<unsigned>(seed);
   s.seed_hi = static_cast<unsigned>(seed >> 32);
   static thread_local DevState<R> staged;  // pinned copy not needed: synchronous below
   staged = s;
   CK(cudaMemcpyAsync(c->d_state, &staged, sizeof(s), cudaMemcpyHostToDevice, c->stream));
   const DevState<R> *S = reinterpret_cast<const DevState<R> *>(c->d_state);
-  if (s.max_in_flight < 0) {
+  if (cost_cap) {
+    prim_cost_kernel<R><<<1, kCostScanThreads, 0, c->stream>>>(S, c->d_pcost);
+  } else if (s.max_in_flight < 0) {
     CK(cudaMemsetAsync(&c->d_ctl->emax_bits, 0, sizeof(unsigned), c->stream));
     if (n > 0) prim_emax_kernel<R><<<static_cast<int>(std::min<long long>((n + 255) / 256, 4 * c->sm_count)), 256, 0,
                                      c->stream>>>(S);
@@ -2201,6 +2320,8 @@ void gv_destroy(void *ctx) {
   cudaFree(c->d_escape);
   cudaFree(c->d_evcnt);
   cudaFree(c->d_evlive);
+  cudaFree(c->d_evcost);
+  cudaFree(c->d_pcost);
   cudaFree(c->d_prim);
   cudaFree(c->d_order);
   cudaFree(c->d_req);

@@ -226,6 +226,29 @@ def test_integer_counts_invariant_to_launch_shape(gvmod):
         ctx.close()
 
 
+def test_automatic_cap_budgets_each_event_by_its_energy(gvmod):
+    """The automatic events-in-flight cap budgets every event by its own
+    primaries (0.15 live tracks per MeV + 64).  With one 100 GeV primary
+    among 100 MeV ones, a 131,072-track queue takes the light events nearly
+    all at once, where a cap sized by the most energetic primary (8 events)
+    needs many times the generations.  The results are those of the other
+    cap, and nothing overflows."""
+    wl = W.pbps_electrons(600, 100.0)
+    wl.primaries["E"][0] = 100_000.0
+    cap = 1 << 17
+    out = {}
+    for name, kw in (("auto", {}), ("fixed", dict(max_events_in_flight=8))):
+        ctx = _ctx(gvmod, wl, per_event_counts=1, stack_capacity=cap, **kw)
+        out[name] = ctx.transport(per_event=True)
+        ctx.close()
+        assert out[name]["status"] == 0, name
+    a, f = out["auto"], out["fixed"]
+    assert np.array_equal(a["counts"][:, :11], f["counts"][:, :11])
+    assert a["counters"]["live_peak"] <= cap
+    assert 3 * a["counters"]["generations"] < f["counters"]["generations"], (
+        a["counters"]["generations"], f["counters"]["generations"])
+
+
 # ---------------------------------------------------------------- edge cases and failures
 def test_edge_cases(gvmod):
     wl = W.pbps_electrons(4, 100.0)
@@ -254,10 +277,15 @@ def test_edge_cases(gvmod):
 
 def test_failure_statuses_are_reported_without_hanging(gvmod):
     wl = W.pbps_electrons(50, 10_000.0)
-    ctx = _ctx(gvmod, wl, stack_capacity=2048)
+    # without a cap, 50 showers of 10 GeV at once overflow a 2048-track queue
+    ctx = _ctx(gvmod, wl, stack_capacity=2048, max_events_in_flight=0)
     with pytest.raises(gvmod.GvError, match="overflow"):
         ctx.transport()
     assert ctx.last_result.status == -4
+    # the automatic cap budgets 1564 tracks to a 10 GeV event: one at a time fits
+    auto = _ctx(gvmod, wl, stack_capacity=2048)
+    assert auto.transport()["status"] == 0
+    auto.close()
     ctx2 = _ctx(gvmod, wl, max_generations=3)
     with pytest.raises(gvmod.GvError, match="budget"):
         ctx2.transport()

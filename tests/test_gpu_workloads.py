@@ -128,9 +128,11 @@ def test_pbps_mixed_types_measured(gvmod):
 
 def test_wsi_100GeV_cells_full_size(gvmod, oracle_mod):
     """1e4 x 100 GeV e- on W/Si with 32x32 cells: the whole run on the GPU,
-    the oracle on the first 1000 events."""
+    the oracle on the first 1000 events.  The queues are sized for the
+    workload's peak (2^25 tracks per type and parity, 12.9 GB): with them
+    about 2200 of the 100 GeV showers are in flight at once."""
     wl = W.standard(W.WSI_100GEV)
-    cap = 1 << 23
+    cap = 1 << 25
     r = _run(gvmod, wl, stack_capacity=cap)
     c = r["counters"]
     assert c["live_peak"] <= cap

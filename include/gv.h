@@ -242,10 +242,13 @@ int gv_build_tables(void *ctx);
  * host tally buffers that are not page-locked the copies, and so the call,
  * finish before it returns.  A second transport on the same context first
  * completes the previous one (filling its result record).  The caller's
- * buffers must stay valid until then.  Returns GV_OK or an error found
- * before the work started (GV_ERR_BAD_ARG, GV_ERR_NO_TABLES, GV_ERR_OOM,
- * GV_ERR_CUDA); errors of the transport itself (GV_ERR_STACK_FULL,
- * GV_ERR_TIMEOUT, GV_ERR_NUMERIC) come from gv_sync. */
+ * buffers must stay valid until then.  Transports of different contexts
+ * on one GPU run one after another on the GPU (their kernels read the
+ * transport's state from one constant-memory record per precision and GPU);
+ * the calls themselves may come from any threads.  Returns GV_OK or an error
+ * found before the work started (GV_ERR_BAD_ARG, GV_ERR_NO_TABLES,
+ * GV_ERR_OOM, GV_ERR_CUDA); errors of the transport itself
+ * (GV_ERR_STACK_FULL, GV_ERR_TIMEOUT, GV_ERR_NUMERIC) come from gv_sync. */
 int gv_transport(void *ctx, const gv_primary *p, long long n, long long n_events,
                  unsigned long long seed, void *stream, gv_result *res);
 
@@ -270,9 +273,10 @@ int gv_transport_events(void *ctx, const gv_primary *p, long long n, long long f
  * that every GPU holds from the library's first use on it until the process
  * exits.  Every call asks the runtime for that array's device address on the
  * current device (a device reset gives it a new one).  Every call reuses the
- * array and clears what must start at zero; calls whose work overlaps on the
- * GPU (two streams, two threads, or a concurrent call on another context)
- * race on it.  The call waits on the host between its launches, so it cannot
+ * array and clears what must start at zero.  Like gv_transport it takes the
+ * GPU's constant-memory state record in turn with every other transport,
+ * and holds it until it returns: calls from several threads, streams or
+ * contexts run one after another and do not share the array's contents.  The call waits on the host between its launches, so it cannot
  * run on a stream that is being captured (GV_ERR_BAD_ARG) and must not run
  * while another stream of the device captures in global mode.
  *   prim      device array of n primaries;

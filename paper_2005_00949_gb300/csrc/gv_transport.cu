@@ -16,7 +16,9 @@
 // Host side: gv_transport enqueues one transport on the context's stream,
 // ordered after the caller's stream (which then waits for it), and returns;
 // gv_sync waits for it and fills the caller's result record from the
-// control block copied back to pinned memory.
+// control block copied back to pinned memory.  The step kernels read the
+// transport's state record from constant memory, one copy per precision and
+// GPU; transports of different contexts on one GPU take turns on it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -759,6 +761,23 @@ template <typename R> __global__ void prim_emax_kernel(const DevState<R> *S) {
   if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(&S->ctl->emax_bits, __float_as_uint(m));
 }
 
+// ------------------------------------------------------------------ the transport's state
+// The step kernels read the transport's state record (queue and tally
+// pointers, seeds, switches) from a constant-memory copy, one per precision
+// and GPU: its fields are then instruction operands, which costs no load and
+// no register on the step path (2.7 % of the benchmark's kernel time against
+// the same record read through a global pointer).  The host fills the copy
+// on the transport's stream from the record in device memory; transports of
+// different contexts on one GPU take turns on it (StateSlot).  The split
+// pipeline's kernels read the device-memory record through their pointer:
+// with them on the constant copy as well, the fused step kernel measured
+// 1.1 % slower.
+__constant__ DevState<float> c_state_f;
+__constant__ DevState<double> c_state_d;
+template <typename R> __device__ __forceinline__ const DevState<R> *tstate();
+template <> __device__ __forceinline__ const DevState<float> *tstate<float>() { return &c_state_f; }
+template <> __device__ __forceinline__ const DevState<double> *tstate<double>() { return &c_state_d; }
+
 // ------------------------------------------------------------------ the kernel
 // Register budget: GV_MIN_BLOCKS resident 256-thread blocks per SM in FP32
 // (measured: with the along-step loop 2 blocks at up to 128 registers beat
@@ -781,7 +800,8 @@ template <typename R> __global__ void prim_emax_kernel(const DevState<R> *S) {
 
 template <typename R, bool SORT, bool MERGE, bool FIELD>
 __global__ void GV_STEP_BOUNDS
-    step_kernel(const DevState<R> *__restrict__ S, int parity) {
+    step_kernel(int parity) {
+  const DevState<R> *__restrict__ S = tstate<R>();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ View<R> sV;
   __shared__ BlockCnt bc;
@@ -1736,7 +1756,7 @@ template <typename R> View<R> make_view(const Ctx *c) {
   return v;
 }
 
-template <typename R> using StepFn = void (*)(const DevState<R> *, int);
+template <typename R> using StepFn = void (*)(int);
 
 // The step kernel compiled for this configuration: basketizer or not, merged
 // or direct scoring, with or without the field propagation.
@@ -1746,8 +1766,59 @@ template <typename R> StepFn<R> pick_step_kernel(const gv_config &c, bool field)
   return c.scoring ? step_kernel<R, false, true, false> : step_kernel<R, false, false, false>;
 }
 
+// The constant-memory state record of each precision and GPU (c_state_f,
+// c_state_d) is shared by every context on that GPU.  A transport takes it
+// on its stream once the previous transport of any context has released it
+// (an event), fills it from its record in device memory, and releases it
+// when everything it queued is on the stream.  The host lock orders the
+// takes; the events order the uses on the GPU, so transports of different
+// contexts on one GPU run one after another.
+constexpr int kMaxDevices = 64;
+std::mutex &slot_mutex() {
+  static std::mutex m;
+  return m;
+}
+cudaEvent_t g_slot_free[2][kMaxDevices];  // [FP64][device]
+
+// Made with a context (gv_setup allocates anyway), so that the
+// allocation-free entry point never creates one.
+cudaError_t slot_event_create(int device, bool fp64) {
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(slot_mutex());
+  cudaEvent_t &e = g_slot_free[fp64 ? 1 : 0][device];
+  if (e) return cudaSuccess;
+  return cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+}
+
+template <typename R> class StateSlot {
+ public:
+  StateSlot(int device, cudaStream_t st)
+      : lk_(slot_mutex()), st_(st), ev_(g_slot_free[sizeof(R) == 8 ? 1 : 0][device]) {}
+  StateSlot(const StateSlot &) = delete;
+  StateSlot &operator=(const StateSlot &) = delete;
+  // wait for the previous user, then copy the record into the slot
+  cudaError_t take(const DevState<R> *record) {
+    if (!ev_) return cudaErrorInvalidResourceHandle;
+    const cudaError_t e = cudaStreamWaitEvent(st_, ev_, 0);
+    if (e != cudaSuccess) return e;
+    if constexpr (sizeof(R) == 8)
+      return cudaMemcpyToSymbolAsync(c_state_d, record, sizeof(DevState<R>), 0, cudaMemcpyDeviceToDevice, st_);
+    else
+      return cudaMemcpyToSymbolAsync(c_state_f, record, sizeof(DevState<R>), 0, cudaMemcpyDeviceToDevice, st_);
+  }
+  ~StateSlot() {
+    if (ev_) cudaEventRecord(ev_, st_);  // also after an error: what was queued is covered
+  }
+
+ private:
+  std::unique_lock<std::mutex> lk_;
+  cudaStream_t st_;
+  cudaEvent_t ev_;
+};
+
 template <typename R> int prepare_device(Ctx *c) {
   CK(cudaSetDevice(c->device));
+  CK(slot_event_create(c->device, sizeof(R) == 8));
   int rc = upload_tables<R>(c);
   if (rc) return rc;
   rc = setup_l2_window(c);
@@ -1890,7 +1961,7 @@ template <typename R> cudaError_t record_generations(Ctx *c) {
     lc.attrs = attr;
     lc.numAttrs = (c->cfg.pdl && i > 0) ? 1 : 0;  // overlap with the previous generation's tail
     const int parity = i & 1;
-    const cudaError_t e = cudaLaunchKernelEx(&lc, step, static_cast<const DevState<R> *>(S), parity);
+    const cudaError_t e = cudaLaunchKernelEx(&lc, step, parity);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -2101,6 +2172,8 @@ int run_transport(Ctx *c, const gv_primary *p, long long n, long long first_even
   staged = s;
   CK(cudaMemcpyAsync(c->d_state, &staged, sizeof(s), cudaMemcpyHostToDevice, c->stream));
   const DevState<R> *S = reinterpret_cast<const DevState<R> *>(c->d_state);
+  StateSlot<R> slot(c->device, c->stream);  // held until every launch below is queued
+  CK(slot.take(S));
   if (cost_cap) {
     prim_cost_kernel<R><<<1, kCostScanThreads, 0, c->stream>>>(S, c->d_pcost);
   } else if (s.max_in_flight < 0) {
@@ -2509,7 +2582,9 @@ extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long 
   s.seed_lo = static_cast<unsigned>(seed);
   s.seed_hi = static_cast<unsigned>(seed >> 32);
   DevState<float> *S = reinterpret_cast<DevState<float> *>(base + kStaticStateOff);
+  StateSlot<float> slot(c->device, st);  // held until the last generation is queued
   static_state_kernel<<<1, 1, 0, st>>>(s, S);
+  if (slot.take(S) != cudaSuccess) return GV_ERR_CUDA;
   if (n > 0)
     prim_emax_kernel<float><<<static_cast<int>(std::min<long long>((n + 255) / 256, 4 * c->sm_count)), 256, 0, st>>>(S);
   init_kernel<float><<<1, 1, 0, st>>>(S);
@@ -2517,7 +2592,7 @@ extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long 
   int between = 1;
   for (;;) {
     for (int i = 0; i < 2 * between; ++i)
-      step_kernel<float, false, false, false><<<grid, c->cfg.block_size, smem, st>>>(S, i & 1);
+      step_kernel<float, false, false, false><<<grid, c->cfg.block_size, smem, st>>>(i & 1);
     if (cudaGetLastError() != cudaSuccess) return GV_ERR_CUDA;
     if (cudaMemcpyAsync(c->h_ctl, s.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)

@@ -1793,7 +1793,8 @@ cudaError_t slot_event_create(int device, bool fp64) {
 template <typename R> class StateSlot {
  public:
   StateSlot(int device, cudaStream_t st)
-      : lk_(slot_mutex()), st_(st), ev_(g_slot_free[sizeof(R) == 8 ? 1 : 0][device]) {}
+      : lk_(slot_mutex()), st_(st),
+        ev_(device >= 0 && device < kMaxDevices ? g_slot_free[sizeof(R) == 8 ? 1 : 0][device] : nullptr) {}
   StateSlot(const StateSlot &) = delete;
   StateSlot &operator=(const StateSlot &) = delete;
   // wait for the previous user, then copy the record into the slot

@@ -434,18 +434,21 @@ def test_largest_geometry_and_material_set(gvmod, oracle_mod):
 
 # ---------------------------------------------------------------- concurrency
 def test_contexts_transport_concurrently(gvmod):
-    """Two contexts driven from two host threads at once (each with its own
-    work stream and buffers) give the results they give one at a time."""
+    """Three contexts driven from three host threads at once (each with its
+    own work stream and buffers; two mixed-precision ones, which take the
+    GPU's mixed state record in turn, and an FP64 one, which has its own)
+    give the results they give one at a time."""
     import threading
-    wls = [W.pbps_electrons(200, 3000.0), W.with_msc(W.pblar_testem3(100, 3000.0))]
-    ctxs = [_ctx(gvmod, wl, per_event_counts=1) for wl in wls]
+    wls = [W.pbps_electrons(200, 3000.0), W.with_msc(W.pblar_testem3(100, 3000.0)), W.pbps_electrons(100, 1000.0)]
+    ctxs = [_ctx(gvmod, wl, per_event_counts=1) for wl in wls[:2]]
+    ctxs.append(_ctx(gvmod, wls[2], per_event_counts=1, precision=1))
     alone = [c.transport(per_event=True) for c in ctxs]
-    both = [None, None]
+    both = [None, None, None]
 
     def run(i):
         both[i] = ctxs[i].transport(per_event=True)
 
-    th = [threading.Thread(target=run, args=(i,)) for i in range(2)]
+    th = [threading.Thread(target=run, args=(i,)) for i in range(3)]
     for t in th:
         t.start()
     for t in th:

@@ -143,3 +143,52 @@ def test_static_transport_refuses_a_capturing_stream(env):
     torch.cuda.synchronize()
     rc, _, _, _, _ = _static_call(torch, gv, ctx, wl, 1, repeats=1)
     assert rc == 0
+
+
+def test_static_transport_takes_turns_with_other_transports(env):
+    """The step kernels read the transport's state from one constant-memory
+    record per GPU, which every transport takes in turn: a static call on
+    one context and gv_transport on another, driven from two host threads
+    on two streams at once, give the results each gives alone."""
+    import threading
+    torch, gv = env
+    wl_a = W.pbps_electrons(200, 2000.0)
+    wl_b = W.with_msc(W.pblar_testem3(100, 3000.0))
+    ctx_a = gv.Context(wl_a, gv.gv_default_config(stack_capacity=1 << 20, process_sort=0, claim_chunks=0))
+    ctx_b = gv.Context(wl_b, gv.gv_default_config(stack_capacity=1 << 20, per_event_counts=1))
+    dev = torch.device("cuda")
+    prim = torch.from_numpy(wl_a.primaries.view(np.uint8).copy()).to(dev)
+    s_a = torch.cuda.Stream()
+
+    def static_run():
+        edep = torch.zeros((wl_a.n_events, ctx_a.n_subtotal), dtype=torch.float64, device=dev)
+        esc = torch.zeros(wl_a.n_events, dtype=torch.float64, device=dev)
+        counters = (C.c_ulonglong * 16)()
+        torch.cuda.synchronize()
+        rc = ctx_a.lib.gv_transport_static(ctx_a.h, prim.data_ptr(), len(wl_a.primaries), wl_a.n_events,
+                                           C.c_ulonglong(wl_a.seed), s_a.cuda_stream, edep.data_ptr(),
+                                           esc.data_ptr(), counters)
+        s_a.synchronize()
+        return rc, edep.cpu().numpy(), list(counters)
+
+    alone_a = static_run()
+    alone_b = ctx_b.transport(per_event=True)
+    both = [None, None]
+
+    def run_a():
+        both[0] = static_run()
+
+    def run_b():
+        both[1] = ctx_b.transport(per_event=True)
+
+    th = [threading.Thread(target=run_a), threading.Thread(target=run_b)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert alone_a[0] == 0 and both[0][0] == 0
+    assert both[0][2][:11] == alone_a[2][:11]
+    assert np.allclose(both[0][1], alone_a[1], rtol=1e-9, atol=1e-9)
+    assert both[1]["status"] == 0
+    assert np.array_equal(both[1]["counts"][:, :11], alone_b["counts"][:, :11])
+    assert np.allclose(both[1]["edep"], alone_b["edep"], rtol=1e-9, atol=1e-9)

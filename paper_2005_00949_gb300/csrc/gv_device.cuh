@@ -640,7 +640,7 @@ template <typename R> __device__ __forceinline__ void at_rest(Kids<R> &k, R u6, 
 // diverges only for the kinematics.  Angles use forms of 1 -+ cos(theta)
 // without cancellation, written from the sampled xi; they are algebraically
 // the textbook two-body kinematics.
-template <typename R>
+template <typename R, bool REJECT = true>
 __device__ int interact(const View<R> &V, int type, int p, R &E, R d[3], const R *u, const RngKey &g, Kids<R> &kids,
                         R &local, int &npair, int &nann) {
   const R ME = static_cast<R>(kME);
@@ -668,7 +668,7 @@ __device__ int interact(const View<R> &V, int type, int p, R &E, R d[3], const R
   }
   R xi = R(0), v = R(0);
   if (model >= 0)
-    v = (model <= kBrem && E >= V.rc.rej_min[model]) ? reject_sample<R>(V, model, E, g, &xi)
+    v = (REJECT && model <= kBrem && E >= V.rc.rej_min[model]) ? reject_sample<R>(V, model, E, g, &xi)
                                                        : alias_sample<R>(V, model, E, u[2], u[3], u[4], &xi);
   R sp, cp;
   m_sincos(static_cast<R>(2.0 * kPi) * u[5], &sp, &cp);

@@ -59,7 +59,9 @@ template <typename R> __device__ __forceinline__ void kahan_add(R &sum, R &comp,
   sum = t;
 }
 
-template <typename R>
+// EXT: compiled with the cell histogram and the per-event counters; a
+// kernel without them serves contexts that have neither.
+template <typename R, bool EXT = true>
 __device__ __forceinline__ void deposit(const View<R> &V, const DevState<R> *S, unsigned ev, int sub, double px,
                                         double py, R dE, Pending<R> *pd = nullptr) {
   if (!(dE != R(0)) || sub < 0) return;
@@ -78,7 +80,7 @@ __device__ __forceinline__ void deposit(const View<R> &V, const DevState<R> *S, 
   } else {
     atomicAdd(&S->edep[key], f2d(dE));
   }
-  if (S->cell) {
+  if (EXT && S->cell) {
     const GeoConst &g = V.geo;
     const int layer = sub / g.nsub_layer;
     // the offset from the wall in FP64, the cell index in FP32 (a cell
@@ -110,10 +112,10 @@ template <typename R> __device__ __forceinline__ void warp_flush(const DevState<
   p.key = kNoKey;
 }
 
-template <typename R>
+template <typename R, bool EXT = true>
 __device__ __forceinline__ void count(const DevState<R> *S, BlockCnt *bc, unsigned ev, int c, unsigned long long n = 1) {
   atomicAdd(&bc->c[c], n);
-  if (S->evcnt) atomicAdd(&S->evcnt[static_cast<size_t>(ev) * GV_NCOUNT + c], n);
+  if (EXT && S->evcnt) atomicAdd(&S->evcnt[static_cast<size_t>(ev) * GV_NCOUNT + c], n);
 }
 
 template <typename R> struct Trk {
@@ -156,7 +158,7 @@ template <typename R> __device__ __noinline__ int integral_choice(const View<R> 
 // keeps its registers for the rest of the step).  OPTS: compiled with the
 // optional processes (multiple scattering, the integral approach); the plain
 // kernel leaves their code out.
-template <typename R, bool FIELD, bool OPTS>
+template <typename R, bool FIELD, bool OPTS, bool EXT>
 __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kids<R> &kids, uint32_t &kk,
                           BlockCnt *bc, int &proc_out, R *u, int &lim_out, Pending<R> *pd) {
   kids.n = 0;
@@ -172,11 +174,11 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   bool have_r0 = false;
   const R tcut = V.rc.tcut;
   if (t.E < tcut) {  // PreStep: tracking cut
-    deposit(V, S, t.ev, t.sub, t.x, t.y, t.E, pd);
+    deposit<R, EXT>(V, S, t.ev, t.sub, t.x, t.y, t.E, pd);
     if (t.type == 2) {
       const uint4 r1 = philox4x32_10(make_uint4(idlo, idhi, k, 1u), key0, key1);
       at_rest(kids, u24<R>(r1.z), u24<R>(r1.w));
-      count(S, bc, t.ev, GV_C_ANNIH);
+      count<R, EXT>(S, bc, t.ev, GV_C_ANNIH);
     }
     return 0;
   }
@@ -224,7 +226,7 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   lim_out = lim;
   if (!(s < INF)) {
     atomicAdd(&S->escape[t.ev], f2d(t.E));
-    if (t.type == 2) count(S, bc, t.ev, GV_C_EP_ESC);
+    if (t.type == 2) count<R, EXT>(S, bc, t.ev, GV_C_EP_ESC);
     return 0;
   }
   // Propagation: FP64 positions, advanced by displacements s d formed in R
@@ -235,7 +237,7 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   if (FIELD && charged && V.rc.field_k != R(0)) {  // the helix of the pre-step momentum
     const R d0[3] = {t.u, t.v, t.w};
     R dp[3], nd[3];
-    if (S->cell) {
+    if (EXT && S->cell) {
       helix(V, t.type, t.E, R(0.5) * s, d0, dp, nd);
       mx = t.x + f2d(dp[0]);
       my = t.y + f2d(dp[1]);
@@ -253,7 +255,7 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
     t.v = nd[1];
     t.w = nd[2];
   } else {
-    if (S->cell) {
+    if (EXT && S->cell) {
       mx = t.x + f2d(R(0.5) * s * t.u);
       my = t.y + f2d(R(0.5) * s * t.v);
     }
@@ -270,7 +272,7 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   t.step = k + 1;
   // the block's step counters are summed per warp by the caller; only the
   // optional per-event rows are booked here
-  if (S->evcnt) {
+  if (EXT && S->evcnt) {
     atomicAdd(&S->evcnt[static_cast<size_t>(t.ev) * GV_NCOUNT + GV_C_STEPS], 1ull);
     atomicAdd(&S->evcnt[static_cast<size_t>(t.ev) * GV_NCOUNT + GV_C_STEPS_G + t.type], 1ull);
   }
@@ -279,14 +281,14 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   // AlongStepAction
   if (charged) {
     const R Ep = eloss_at(V, mat, t.type, t.E, gi, gf, s, Rr);
-    deposit(V, S, t.ev, pre_sub, mx, my, t.E - Ep, pd);
+    deposit<R, EXT>(V, S, t.ev, pre_sub, mx, my, t.E - Ep, pd);
     t.E = Ep;
     if (t.E < tcut) {
-      deposit(V, S, t.ev, pre_sub, t.x, t.y, t.E, pd);
+      deposit<R, EXT>(V, S, t.ev, pre_sub, t.x, t.y, t.E, pd);
       if (t.type == 2) {
         const uint4 r1 = philox4x32_10(make_uint4(idlo, idhi, k, 1u), key0, key1);
         at_rest(kids, u24<R>(r1.z), u24<R>(r1.w));
-        count(S, bc, t.ev, GV_C_ANNIH);
+        count<R, EXT>(S, bc, t.ev, GV_C_ANNIH);
       }
       return 0;
     }
@@ -304,9 +306,9 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
   if (lim == 0) {
     if (next < 0) {
       atomicAdd(&S->escape[t.ev], f2d(t.E));
-      if (t.type == 2) count(S, bc, t.ev, GV_C_EP_ESC);
+      if (t.type == 2) count<R, EXT>(S, bc, t.ev, GV_C_EP_ESC);
       if ((t.flags & kFlagPrimary) && !(t.flags & kFlagInteracted) && plane == V.geo.nsub)
-        count(S, bc, t.ev, GV_C_UNSCAT);
+        count<R, EXT>(S, bc, t.ev, GV_C_UNSCAT);
       return 0;
     }
     t.sub = next;
@@ -345,7 +347,7 @@ __device__ int step_track(const View<R> &V, const DevState<R> *S, Trk<R> &t, Kid
 // state, the local deposit and the counters.  Returns 1 if the particle
 // survives, 0 if it ended, -1 if the process was kinematically closed at the
 // post-step energy (nothing changes).
-template <typename R, bool OPTS = true>
+template <typename R, bool OPTS = true, bool EXT = true>
 __device__ __forceinline__ int final_state(const View<R> &V, const DevState<R> *S, BlockCnt *bc, int type, int proc,
                                            R &E, R d[3], const R *u, Kids<R> &kids, unsigned ev, int sub,
                                            double x, double y, unsigned long long id, uint32_t kk,
@@ -356,9 +358,9 @@ __device__ __forceinline__ int final_state(const View<R> &V, const DevState<R> *
                     S->seed_hi};
   const int r = interact<R, OPTS>(V, type, proc, E, d, u, g, kids, local, np, na);
   if (r < 0) return -1;
-  if (np) count(S, bc, ev, GV_C_PAIR, np);
-  if (na) count(S, bc, ev, GV_C_ANNIH, na);
-  deposit(V, S, ev, sub, x, y, local, pd);
+  if (np) count<R, EXT>(S, bc, ev, GV_C_PAIR, np);
+  if (na) count<R, EXT>(S, bc, ev, GV_C_ANNIH, na);
+  deposit<R, EXT>(V, S, ev, sub, x, y, local, pd);
   return r;
 }
 
@@ -439,7 +441,7 @@ template <typename R> struct LocalStack {
 // PostStepActions: append the step's secondaries to the output queues, or,
 // with a local stack, to the block's stack while it has room.  Called by all
 // 32 lanes of a converged warp (lanes without secondaries pass kids.n == 0).
-template <typename R>
+template <typename R, bool EXT = true>
 __device__ void push_kids(const DevState<R> *S, int out, const Parent &t, const Kids<R> &kids, uint32_t kk,
                           BlockCnt *bc, const LocalStack<R> *ls = nullptr) {
   const unsigned any = __ballot_sync(0xffffffffu, kids.n > 0);
@@ -474,7 +476,7 @@ __device__ void push_kids(const DevState<R> *S, int out, const Parent &t, const 
       e.sub = t.sub;
       e.type = kids.type[j];
       atomicAdd(&bc->c[GV_C_TRK_G + kids.type[j]], 1ull);
-      if (S->evcnt) atomicAdd(&S->evcnt[static_cast<size_t>(t.ev) * GV_NCOUNT + GV_C_TRK_G + kids.type[j]], 1ull);
+      if (EXT && S->evcnt) atomicAdd(&S->evcnt[static_cast<size_t>(t.ev) * GV_NCOUNT + GV_C_TRK_G + kids.type[j]], 1ull);
       local |= 1u << j;
     }
   }
@@ -499,7 +501,7 @@ __device__ void push_kids(const DevState<R> *S, int out, const Parent &t, const 
                                     (static_cast<unsigned long long>(w[2 * j + 1]) << 32);
       store(S->q[out][q], slot, t.x, t.y, t.z, kids.d[j][0], kids.d[j][1], kids.d[j][2], kids.E[j], R(-1), id, t.ev,
             0u, t.sub);
-      if (S->evcnt) atomicAdd(&S->evcnt[static_cast<size_t>(t.ev) * GV_NCOUNT + GV_C_TRK_G + q], 1ull);
+      if (EXT && S->evcnt) atomicAdd(&S->evcnt[static_cast<size_t>(t.ev) * GV_NCOUNT + GV_C_TRK_G + q], 1ull);
       ++slot;
     }
   }
@@ -800,7 +802,7 @@ template <> __device__ __forceinline__ const DevState<double> *tstate<double>() 
 #define GV_STEP_BOUNDS __launch_bounds__(GV_MAX_BLOCK, sizeof(R) == 4 ? GV_MIN_BLOCKS : 1)
 #endif
 
-template <typename R, bool SORT, bool MERGE, bool FIELD, bool OPTS>
+template <typename R, bool SORT, bool MERGE, bool FIELD, bool OPTS, bool EXT>
 __global__ void GV_STEP_BOUNDS
     step_kernel(int parity) {
   const DevState<R> *__restrict__ S = tstate<R>();
@@ -970,10 +972,10 @@ __global__ void GV_STEP_BOUNDS
       t.step = 0;
       t.flags = kFlagPrimary;
       t.sub = locate(V.zb, V.geo.nsub, p.z, p.w);
-      count(S, &bc, t.ev, GV_C_TRK_G + t.type);
+      count<R, EXT>(S, &bc, t.ev, GV_C_TRK_G + t.type);
       if (t.sub < 0) {
         atomicAdd(&S->escape[t.ev], p.E_MeV);
-        if (t.type == 2) count(S, &bc, t.ev, GV_C_EP_ESC);
+        if (t.type == 2) count<R, EXT>(S, &bc, t.ev, GV_C_EP_ESC);
         primary_cost(S, t.ev, e_in, false);
       } else {
         alive = true;
@@ -1020,7 +1022,7 @@ __global__ void GV_STEP_BOUNDS
       for (int m = 0; m < inner && alive && proc < 0; ++m) {
         ++n_iter;
         const uint32_t before = t.step;
-        alive = step_track<R, FIELD, OPTS>(V, S, t, kids, kstep, &bc, proc, u, lim, pd) != 0;
+        alive = step_track<R, FIELD, OPTS, EXT>(V, S, t, kids, kstep, &bc, proc, u, lim, pd) != 0;
         // NaN energy, or a non-finite z (tested on its exponent bits: an FP64
         // comparison would take the FP64 pipe)
         if (!(t.E == t.E) || (__double2hiint(t.z) & 0x7ff00000) == 0x7ff00000) {
@@ -1035,14 +1037,14 @@ __global__ void GV_STEP_BOUNDS
       }
       if (!SORT && alive && proc >= 0) {  // final state in place (warp-divergent across processes)
         R d[3] = {t.u, t.v, t.w};
-        const int r = final_state<R, OPTS>(V, S, &bc, t.type, proc, t.E, d, u, kids, t.ev, t.sub, t.x, t.y, t.id, kstep, pd);
+        const int r = final_state<R, OPTS, EXT>(V, S, &bc, t.type, proc, t.E, d, u, kids, t.ev, t.sub, t.x, t.y, t.id, kstep, pd);
         if (r >= 0) {
           t.u = d[0]; t.v = d[1]; t.w = d[2];
           t.flags |= kFlagInteracted;
           alive = r != 0;
         }
       }
-      push_kids(S, out, parent_of(t), kids, kstep, &bc);
+      push_kids<R, EXT>(S, out, parent_of(t), kids, kstep, &bc);
       if (MERGE) warp_flush(S, pend);
       {  // step counters, one shared-memory atomic per warp and kind
         const unsigned wst = __reduce_add_sync(0xffffffffu, n_st);
@@ -1127,7 +1129,7 @@ __global__ void GV_STEP_BOUNDS
           R d[3] = {q.d0, q.d1, q.d2};
           R e = q.E;
           const int ty = q.tp / 3;
-          const int r = final_state<R, OPTS>(V, S, &bc, ty, q.tp - 3 * ty, e, d, uu, kb, q.ev, q.sub, q.x, q.y, q.id, q.kk);
+          const int r = final_state<R, OPTS, EXT>(V, S, &bc, ty, q.tp - 3 * ty, e, d, uu, kb, q.ev, q.sub, q.x, q.y, q.id, q.kk);
           par.x = q.x; par.y = q.y; par.z = q.z;
           par.id = q.id;
           par.ev = q.ev;
@@ -1136,7 +1138,7 @@ __global__ void GV_STEP_BOUNDS
           q.E = e; q.d0 = d[0]; q.d1 = d[1]; q.d2 = d[2];
           q.tp = r;
         }
-        push_kids(S, out, par, kb, pk, &bc, use_local ? &lstk : nullptr);
+        push_kids<R, EXT>(S, out, par, kb, pk, &bc, use_local ? &lstk : nullptr);
         __syncthreads();
         if (key >= 0) {
           const IReq<R> &q = req[slot];
@@ -1357,7 +1359,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_ALONG_MIN_BLOCKS : 2)
       for (int m = 0; m < S->along_steps && alive && proc < 0; ++m) {
         ++n_iter;
         const uint32_t before = t.step;
-        alive = step_track<R, true, true>(V, S, t, kids, kstep, &bc, proc, u, lim, static_cast<Pending<R> *>(nullptr)) != 0;
+        alive = step_track<R, true, true, true>(V, S, t, kids, kstep, &bc, proc, u, lim, static_cast<Pending<R> *>(nullptr)) != 0;
         if (!(t.E == t.E) || (__double2hiint(t.z) & 0x7ff00000) == 0x7ff00000) {
           set_status(ctl, GV_ERR_NUMERIC);
           alive = false;
@@ -1762,21 +1764,27 @@ template <typename R> using StepFn = void (*)(int);
 
 // The step kernel compiled for this configuration: basketizer or not, merged
 // or direct scoring, with or without the field propagation.  The basketizing
-// kernel of the default configuration also comes without the code of the
-// optional processes (multiple scattering, the integral approach, rejection
-// sampling): measured 3.1 % faster on the benchmark than the kernel that
-// carries them behind run-time switches.
+// kernel also comes without the code of the optional processes (multiple
+// scattering, the integral approach, rejection sampling), and without the
+// cell histogram and per-event counters, for contexts that use none of
+// them: each cut measured about 3 % on the benchmark against carrying the
+// code behind run-time switches.
 template <typename R> StepFn<R> pick_step_kernel(const Ctx *x) {
   const gv_config &c = x->cfg;
   const bool field = x->geo.field_T != 0.0;
   bool opts = (x->cuts.process_mask & (GV_P_MSC | GV_P_INTEGRAL)) != 0;
   for (int m = 0; m < kNModel; ++m) opts = opts || x->cuts.reject_min_MeV[m] < 1e30;
-  if (field) return c.process_sort ? step_kernel<R, true, false, true, true> : step_kernel<R, false, false, true, true>;
+  // a transport scores cells or per-event counts only if the context has
+  // cells or keeps per-event counts: otherwise both pointers stay null
+  const bool ext = c.per_event_counts != 0 || static_cast<size_t>(x->geo.n_layers) * x->geo.nx_cells * x->geo.ny_cells != 0;
+  if (field)
+    return c.process_sort ? step_kernel<R, true, false, true, true, true> : step_kernel<R, false, false, true, true, true>;
   if (c.process_sort) {
-    if (c.scoring) return step_kernel<R, true, true, false, true>;
-    return opts ? step_kernel<R, true, false, false, true> : step_kernel<R, true, false, false, false>;
+    if (c.scoring) return step_kernel<R, true, true, false, true, true>;
+    if (opts) return step_kernel<R, true, false, false, true, true>;
+    return ext ? step_kernel<R, true, false, false, false, true> : step_kernel<R, true, false, false, false, false>;
   }
-  return c.scoring ? step_kernel<R, false, true, false, true> : step_kernel<R, false, false, false, true>;
+  return c.scoring ? step_kernel<R, false, true, false, true, true> : step_kernel<R, false, false, false, true, true>;
 }
 
 // The constant-memory state record of each precision and GPU (c_state_f,
@@ -2555,11 +2563,11 @@ extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long 
   int rc = static_scratch(&base);
   if (rc) return rc;
   const size_t smem = c->req_off;  // tables and geometry; the non-basketizing kernel
-  if (cudaFuncSetAttribute(step_kernel<float, false, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(step_kernel<float, false, false, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess)
     return GV_ERR_CUDA;
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_kernel<float, false, false, false, true>, c->cfg.block_size, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_kernel<float, false, false, false, true, true>, c->cfg.block_size, smem) !=
           cudaSuccess ||
       occ < 1)
     return GV_ERR_CUDA;
@@ -2606,7 +2614,7 @@ extern "C" int gv_transport_static(void *ctx, const gv_primary *prim, long long 
   int between = 1;
   for (;;) {
     for (int i = 0; i < 2 * between; ++i)
-      step_kernel<float, false, false, false, true><<<grid, c->cfg.block_size, smem, st>>>(i & 1);
+      step_kernel<float, false, false, false, true, true><<<grid, c->cfg.block_size, smem, st>>>(i & 1);
     if (cudaGetLastError() != cudaSuccess) return GV_ERR_CUDA;
     if (cudaMemcpyAsync(c->h_ctl, s.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)

@@ -46,12 +46,12 @@ def _config(world: int) -> dict:
             "l2": "GPU arm: flushed between timed steps (512 MiB write); reference arm (host CPU): not applicable"}
 N_EVENTS = 2000
 E0 = 10_000.0
-# algorithmic DRAM bytes of one track step in a step-synchronous wavefront,
-# as the scope table fixes them for the mixed form: read + write a ~68 B track
-# record (136 B), ~0.2 secondaries of 68 B (14 B), a basket index read and
-# written (8 B)
+# algorithmic DRAM bytes of one track step of the mixed form in a
+# step-synchronous wavefront: read + write a ~68 B track record (136 B),
+# ~0.2 secondaries of 68 B (14 B), a basket index read and written (8 B)
 SCOPE_BYTES_PER_STEP = 158.0
-# the same with this build's record (64 B) and the measured secondaries per step
+# the same count with this library's 64-byte track record and the measured
+# secondaries per step
 TRACK_BYTES = 64
 
 

@@ -226,20 +226,22 @@ def test_integer_counts_invariant_to_launch_shape(gvmod):
         ctx.close()
 
 
-def test_kernel_variants_agree(gvmod):
+@pytest.mark.parametrize("prec", [0, 1], ids=["mixed", "fp64"])
+def test_kernel_variants_agree(gvmod, prec):
     """The basketizing kernel is compiled three ways: without the optional
     processes and without the cell and per-event tallies (contexts that use
     none of them), with those tallies, and with everything.  A rejection
     threshold no energy reaches (1e29 MeV) selects the full kernel without
     changing a history.  The three give the same integer counts, and
-    deposits equal up to the rounding of separately compiled FP32 code."""
+    deposits equal up to the rounding of separately compiled FP32 code (to
+    FP64 summation order in FP64)."""
     import dataclasses
     wl = W.pbps_mixed(120).subset(120)
     wl.primaries["E"] = np.minimum(wl.primaries["E"], 5000.0)
     full = dataclasses.replace(wl, reject_min=(1e29,) * 6)
     runs = {}
     for name, w, kw in (("lean", wl, {}), ("tallies", wl, dict(per_event_counts=1)), ("full", full, {})):
-        ctx = _ctx(gvmod, w, **kw)
+        ctx = _ctx(gvmod, w, precision=prec, **kw)
         runs[name] = ctx.transport(per_event=bool(kw))
         ctx.close()
         assert runs[name]["status"] == 0, name
@@ -249,7 +251,7 @@ def test_kernel_variants_agree(gvmod):
         for k in keys:
             assert runs[name]["counters"][k] == runs["lean"]["counters"][k], (name, k)
         scale = np.maximum(runs["lean"]["edep"].sum(1, keepdims=True), 1.0)
-        assert (np.abs(runs[name]["edep"] - runs["lean"]["edep"]) / scale).max() < 1e-5, name
+        assert (np.abs(runs[name]["edep"] - runs["lean"]["edep"]) / scale).max() < (1e-9 if prec else 1e-5), name
     # the per-event counts of the tallies kernel add up to the global ones
     c = runs["tallies"]["counts"]
     assert c[:, 0].sum() == runs["lean"]["counters"]["steps"]

@@ -150,8 +150,9 @@ typedef struct {
                                      (0.15 per MeV + 64) events, at least 16 */
   int claim_chunks;           /* without process_sort: 1 (default) = every warp claims its own
                                  32-track chunks from 16 sliced counters; 0 = one claim per block */
-  int along_steps;            /* with process_sort: steps a track may take without a discrete
-                                 interaction before its block baskets the interactions (1..64) */
+  int along_steps;            /* with process_sort: steps an electron or positron may take without a
+                                 discrete interaction before its block baskets the interactions
+                                 (1..64; default 3) */
   int scoring;                /* energy tallies (1 is not available with a field):
                                  0 (default) = one FP64 atomic per deposit;
                                  1 = a lane merges consecutive deposits to the same (event,
@@ -179,6 +180,7 @@ typedef struct {
   int blocking;               /* 0 (default): gv_transport returns once the transport is enqueued and
                                  gv_sync completes it; 1: gv_transport returns when it is done, with
                                  its result record filled (device_loop = 0 always behaves so) */
+  int along_steps_photon;     /* the same for photons (1..64; default 5; 0: along_steps) */
 } gv_config;
 
 /* A primary track; layout shared with the seeded input generator.  Its random

@@ -11,7 +11,9 @@ time (median of repeats).  Knobs:
                                     budget below which primaries are injected)
   process_sort                   -- in-block re-basketing by selected process
   claim_chunks                   -- per-block or per-warp work claims
-  along_steps                    -- steps a lane takes before its block baskets
+  along_steps, along_steps_photon
+                                 -- steps a lane takes (charged track, photon)
+                                    before its block baskets
   scoring                        -- direct or warp-merged tally atomics
 Integer results do not depend on any of these (per-track random streams), so
 the tuner only trades time.
@@ -28,6 +30,7 @@ SPACE = {
     "process_sort": [1, 0],
     "claim_chunks": [0, 1],
     "along_steps": [2, 3, 4, 6],
+    "along_steps_photon": [3, 4, 5, 6],
     "scoring": [0, 1],
     "local_stack": [1, 0],
     "pdl": [1, 0],

@@ -109,6 +109,7 @@ template <typename R> struct DevState {
   int grid, adaptive_chunk;  // blocks of the step kernel; spread small populations over all of them
   const unsigned long long *pcost;  // automatic cap: prefix sums of the primaries' track budgets [n_prim + 1], or null
   unsigned long long *evcost;       // automatic cap: budget held by each event in flight [n_events]
+  int along_steps_g;                // basketizer: along-step budget of photons
 };
 
 }  // namespace gv

@@ -1018,7 +1018,10 @@ __global__ void GV_STEP_BOUNDS
       // block then baskets the interactions.  Step tallies stay per lane and
       // are summed per warp afterwards.
       unsigned n_st = 0, n_geom = 0, n_iter = 0;
-      const int inner = SORT ? S->along_steps : 1;
+      // photons cross layers in runs of boundary-limited steps; charged tracks
+      // are stopped more often by their continuous-loss limit: each type has
+      // its own budget (measured best at 5 and 3 on the benchmark)
+      const int inner = SORT ? (t.type == 0 ? S->along_steps_g : S->along_steps) : 1;
       for (int m = 0; m < inner && alive && proc < 0; ++m) {
         ++n_iter;
         const uint32_t before = t.step;
@@ -1356,7 +1359,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? GV_ALONG_MIN_BLOCKS : 2)
       int proc = -1, lim = -1;
       R u[8];
       unsigned n_st = 0, n_geom = 0, n_iter = 0;
-      for (int m = 0; m < S->along_steps && alive && proc < 0; ++m) {
+      const int inner = t.type == 0 ? S->along_steps_g : S->along_steps;
+      for (int m = 0; m < inner && alive && proc < 0; ++m) {
         ++n_iter;
         const uint32_t before = t.step;
         alive = step_track<R, true, true, true>(V, S, t, kids, kstep, &bc, proc, u, lim, static_cast<Pending<R> *>(nullptr)) != 0;
@@ -1592,6 +1596,7 @@ int validate_cfg(const gv_config &c) {
   if (c.max_generations < 1 || c.max_events_in_flight < -1) return GV_ERR_BAD_ARG;
   if (c.claim_chunks < 0 || c.claim_chunks > 1) return GV_ERR_BAD_ARG;
   if (c.along_steps < 1 || c.along_steps > 64) return GV_ERR_BAD_ARG;
+  if (c.along_steps_photon < 0 || c.along_steps_photon > 64) return GV_ERR_BAD_ARG;
   if (c.scoring < 0 || c.scoring > 1) return GV_ERR_BAD_ARG;
   if (c.l2_persist < 0 || c.l2_persist > 1) return GV_ERR_BAD_ARG;
   if (c.local_stack < 0 || c.local_stack > 1) return GV_ERR_BAD_ARG;
@@ -1900,6 +1905,7 @@ template <typename R> DevState<R> make_state(Ctx *c) {
   s.adaptive_chunk = (c->cfg.process_sort && !c->cfg.pipeline) ? 1 : 0;
   s.claim_chunks = c->cfg.claim_chunks;
   s.along_steps = c->cfg.along_steps;
+  s.along_steps_g = c->cfg.along_steps_photon > 0 ? c->cfg.along_steps_photon : c->cfg.along_steps;
   s.scoring = c->cfg.scoring;
   s.pipeline = c->cfg.pipeline;
   s.req = reinterpret_cast<GReq<R> *>(c->d_req);
@@ -2262,8 +2268,9 @@ int gv_default_config(gv_config *cfg) {
   cfg->precision = GV_MIXED;
   cfg->mode = GV_BATCHED;
   // measured on 2000 x 10 GeV e- in Pb/polystyrene (GB300): the basketizing
-  // kernel with block claims, 2 blocks of 256 per SM, up to 4 along-steps per
-  // basket round, one round per claim
+  // kernel with block claims, 2 blocks of 256 per SM, up to 3 along-steps per
+  // basket round for electrons and positrons and 5 for photons, one round
+  // per claim
   cfg->block_size = 256;
   cfg->blocks_per_sm = 2;
   cfg->steps_per_claim = 1;
@@ -2278,7 +2285,8 @@ int gv_default_config(gv_config *cfg) {
   cfg->process_sort = 1;
   cfg->max_events_in_flight = -1;
   cfg->claim_chunks = 0;
-  cfg->along_steps = 4;
+  cfg->along_steps = 3;
+  cfg->along_steps_photon = 5;
   cfg->scoring = 0;
   cfg->l2_persist = 0;
   cfg->pipeline = 0;

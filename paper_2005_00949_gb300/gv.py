@@ -61,7 +61,8 @@ class gv_config(C.Structure):
                 ("process_sort", C.c_int), ("max_events_in_flight", C.c_longlong),
                 ("claim_chunks", C.c_int), ("along_steps", C.c_int), ("scoring", C.c_int),
                 ("l2_persist", C.c_int), ("pipeline", C.c_int), ("local_stack", C.c_int),
-                ("pdl", C.c_int), ("device_loop", C.c_int), ("blocking", C.c_int)]
+                ("pdl", C.c_int), ("device_loop", C.c_int), ("blocking", C.c_int),
+                ("along_steps_photon", C.c_int)]
 
 
 class gv_result(C.Structure):

@@ -132,7 +132,8 @@ def test_argument_validation_without_gpu(lib):
                      dict(stack_capacity=100), dict(refill_batch=0), dict(refill_low_water=-1),
                      dict(generations_per_graph=3), dict(generations_per_graph=0), dict(max_generations=0),
                      dict(max_events_in_flight=-2), dict(claim_chunks=2), dict(along_steps=0),
-                     dict(along_steps=65), dict(scoring=2), dict(l2_persist=-1), dict(local_stack=2),
+                     dict(along_steps=65), dict(along_steps_photon=-1), dict(along_steps_photon=65),
+                     dict(scoring=2), dict(l2_persist=-1), dict(local_stack=2),
                      dict(pdl=2), dict(device_loop=2), dict(pipeline=2), dict(pipeline=1, scoring=1)):
         cfg = gv.gv_default_config(**bad_knob)
         assert lib.gv_setup(C.byref(h), mats, 1, C.byref(geo), C.byref(cuts), C.byref(cfg)) == -1, bad_knob

@@ -131,12 +131,12 @@ def test_wsi_100GeV_cells_full_size(gvmod, oracle_mod):
     the oracle on the first 1000 events.  The queues are sized for the
     workload's peak (2^25 tracks per type and parity, 12.9 GB): with them
     about 2200 of the 100 GeV showers are in flight at once.  Three
-    along-steps per basket round is the autotuner's choice for this
-    workload (the thin silicon gaps make charged steps boundary-limited):
-    6 % faster than the default four, the same histories."""
+    along-steps per basket round for every type is the autotuner's choice
+    for this workload (the thin silicon gaps make charged steps
+    boundary-limited): 6 % faster than four, the same histories."""
     wl = W.standard(W.WSI_100GEV)
     cap = 1 << 25
-    r = _run(gvmod, wl, stack_capacity=cap, along_steps=3)
+    r = _run(gvmod, wl, stack_capacity=cap, along_steps=3, along_steps_photon=3)
     c = r["counters"]
     assert c["live_peak"] <= cap
     per_layer = r["edep"].reshape(wl.n_events, 50, 2).sum((0, 2))

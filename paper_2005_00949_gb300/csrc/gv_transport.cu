@@ -2275,7 +2275,7 @@ int gv_default_config(gv_config *cfg) {
   cfg->blocks_per_sm = 2;
   cfg->steps_per_claim = 1;
   cfg->tail_steps_per_claim = 4;
-  cfg->tail_threshold = 100000;
+  cfg->tail_threshold = 1ll << 15;
   cfg->stack_capacity = 1ll << 23;
   cfg->refill_low_water = 1ll << 21;
   cfg->refill_batch = 1ll << 14;
